@@ -1,0 +1,76 @@
+"""Seeded synthetic inputs for the MPHF build workloads.
+
+This module only draws random inputs; it holds none of the construction's
+arithmetic.  Both the CPU oracle tests and the CUDA path (tests, bench) take
+their inputs from here so that they see exactly the same keys.
+
+The generator is the splitmix64 stream (Steele, Lea, Flood, OOPSLA 2014):
+state_i = seed + i * 0x9E3779B97F4A7C15, output_i = splitmix64-output(state_i),
+i = 1, 2, ...  Uniform doubles in [0, 1) take the top 53 bits.
+
+Workloads (stand-ins for the paper's random-string inputs, Sec. 7):
+  * ``distinct_u64(count, seed)``: the stream's outputs in order, repeats
+    skipped, until ``count`` distinct 64-bit keys.
+  * ``leaf_instances(count, seed)``: independent leaves with sizes
+    40 + floor(U * 25) in [40, 64] and uniform 64-bit keys from the same stream.
+  * ``ascii_strings(count, seed)``: strings of length 10 + floor(U * 41) in
+    [10, 50], bytes uniform in [1, 127].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_PHI = np.uint64(0x9E3779B97F4A7C15)
+_C1 = np.uint64(0xBF58476D1CE4E5B9)
+_C2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64_stream(seed: int, count: int, start: int = 1) -> np.ndarray:
+    """Outputs start .. start+count-1 of the splitmix64 stream from ``seed``."""
+    with np.errstate(over="ignore"):
+        i = np.arange(start, start + count, dtype=np.uint64)
+        z = np.uint64(seed & (2**64 - 1)) + i * _PHI
+        z = (z ^ (z >> np.uint64(30))) * _C1
+        z = (z ^ (z >> np.uint64(27))) * _C2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform01(seed: int, count: int, start: int = 1) -> np.ndarray:
+    return (splitmix64_stream(seed, count, start) >> np.uint64(11)).astype(np.float64) * (2.0**-53)
+
+
+def distinct_u64(count: int, seed: int) -> np.ndarray:
+    """First ``count`` distinct outputs of the stream, in stream order."""
+    out = np.empty(0, np.uint64)
+    start = 1
+    need = count
+    while out.size < count:
+        chunk = splitmix64_stream(seed, need + 16, start)
+        start += chunk.size
+        cand = np.concatenate([out, chunk])
+        _, first = np.unique(cand, return_index=True)
+        out = cand[np.sort(first)][:count]
+        need = count - out.size
+    return out
+
+
+def leaf_instances(count: int, seed: int, lo: int = 40, hi: int = 64):
+    """(keys, offsets): leaf i holds keys[offsets[i]:offsets[i+1]]."""
+    span = hi - lo + 1
+    sizes = lo + np.floor(uniform01(seed, count) * span).astype(np.int64)
+    offs = np.zeros(count + 1, np.int64)
+    np.cumsum(sizes, out=offs[1:])
+    keys = splitmix64_stream(seed, int(offs[-1]), start=count + 1)
+    return keys, offs.astype(np.uint32)
+
+
+def ascii_strings(count: int, seed: int, min_len: int = 10, max_len: int = 50):
+    """(bytes, offsets) of ``count`` random strings, bytes uniform in [1, 127]."""
+    span = max_len - min_len + 1
+    lens = min_len + np.floor(uniform01(seed, count) * span).astype(np.int64)
+    offs = np.zeros(count + 1, np.uint64)
+    np.cumsum(lens, out=offs[1:].view(np.int64))
+    total = int(offs[-1])
+    raw = splitmix64_stream(seed, total, start=count + 1)
+    data = (1 + (raw % np.uint64(127))).astype(np.uint8)
+    return data, offs
