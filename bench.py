@@ -1,0 +1,279 @@
+"""Benchmark: MPHF builds of 10^6 uniform 64-bit keys (splitmix64 stream seed 2),
+leaf size 48, bucket size 2000, on one GB300 per rank.
+
+A step is one whole build (fingerprints, bucket partition, splitting trees,
+leaf seed search, orientation, Golomb-Rice/Elias-Fano encoding, retrieval
+solve) from keys resident in HBM to the encoded MPHF in HBM.  Prints one JSON
+line (rank 0).  Ranks build independent key sets (weak scaling, no collective
+on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_KEYS, LEAF, BUCKET, KEY_SEED = 1_000_000, 48, 2000, 2
+WORKLOAD = "mphf_build_1M_u64_keys_leaf48_bucket2000"
+METRIC = "MPHF build keys/s (1M u64 keys, leaf 48, bucket 2000), leaf seeds tested/s, % integer-issue roofline"
+# integer lane-operations of one key-seed evaluation of the leaf hash + filter
+# (x^c: 2, 64-bit multiply: 3, two range reductions: 2, h1 adjust: 2, two
+# candidate bits into a 64-bit mask held as two words: 8)
+OPS_PER_EVAL_WIDE = 17
+OPS_PER_EVAL_NARROW = 12
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_baseline(sample_keys: int, reps: int = 1):
+    """The oracle as it stands on the host cores, on the first sample_keys keys
+    of the same stream (same leaf and bucket size)."""
+    import oracle
+
+    oracle.build()
+    import shk_inputs
+
+    keys = shk_inputs.distinct_u64(sample_keys, KEY_SEED)
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    for _ in range(reps):
+        oracle.build_mphf(keys, n=LEAF, b=BUCKET, nthreads=cores)
+    dt = time.perf_counter() - t
+    return {"value": sample_keys * reps / dt, "unit": "keys/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {sample_keys} keys of the same stream ({(sample_keys + BUCKET - 1) // BUCKET} buckets), "
+                      f"leaf 48, bucket 2000, OpenMP over buckets, {reps} build(s), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    sample = 24000
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps would only add minutes
+    t = time.perf_counter()
+    base = None
+    for _ in range(args.steps):
+        base = _cpu_baseline(sample)
+    dt = time.perf_counter() - t
+    value = sample * args.steps / dt
+    base["value"] = value
+    line = {"metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "keys": N_KEYS, "leaf_size": LEAF, "bucket_size": BUCKET,
+                       "sample_keys": sample},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import paper_2308_09561_gb300 as pkg
+    import shk_inputs
+
+    pkg.load_library()
+    keys = shk_inputs.distinct_u64(N_KEYS, KEY_SEED + 1000 * rank)
+    dkeys = torch.from_numpy(keys.view(np.int64)).cuda()
+    host_keys = torch.from_numpy(keys.view(np.int64)).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step(profile=True):
+        m = pkg.shk_build(dkeys, LEAF, BUCKET, profile=profile)
+        st = m.stats()
+        m.close()
+        return st
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    stats = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(i)
+            ev[i][0].record(stream)
+            stats.append(step())
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_sum = sum(step_ms) / 1e3
+    if dist:
+        tt = torch.tensor([t_sum], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_sum = float(tt.item())
+    value = N_KEYS * ws * args.steps / t_sum
+
+    # end to end through the public API: pinned host keys in, serialized MPHF out
+    e2e_ms = []
+    blob_bytes = 0
+    for i in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        m = pkg.shk_build(host_keys, LEAF, BUCKET)
+        blob = m.serialize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t))
+        blob_bytes = len(blob)
+        m.close()
+    e2e_value = N_KEYS * ws / (np.mean(e2e_ms) / 1e3)
+
+    leaf_ms = np.mean([s["ms_leaf"] for s in stats])
+    seeds_min = stats[-1]["leaf_seeds_min"]
+    evals = stats[-1]["leaf_key_evals"]
+    peaks = _peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tops = sms * 4 * 32 * sm_max_mhz * 1e6 / 1e12
+    achieved_tops = evals * OPS_PER_EVAL_WIDE / (leaf_ms / 1e3) / 1e12
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_sum / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "keys": N_KEYS, "leaf_size": LEAF, "bucket_size": BUCKET,
+                   "key_stream_seed": KEY_SEED, "schedule": "persistent",
+                   "l2": "256 MB buffer written between timed steps (flush), outside the step events",
+                   "parallelism": f"replicas x{ws}"},
+        "leaf_seeds_per_s": seeds_min / (leaf_ms / 1e3),
+        "leaf_seeds_per_s_build": seeds_min * ws * args.steps / t_sum,
+        "key_seed_evals_per_s": evals / (leaf_ms / 1e3),
+        "bits_per_key": 8 * blob_bytes / N_KEYS,
+        "phase_ms": {k: float(np.mean([s[k] for s in stats])) for k in
+                     ("ms_fingerprint", "ms_partition", "ms_split", "ms_leaf", "ms_orient", "ms_encode",
+                      "ms_ribbon", "ms_total")},
+        "roofline": {"bound": "alu", "kernel": "k_leaf_persistent", "achieved": achieved_tops,
+                     "peak": peak_tops, "unit": "T int-lane-ops/s", "frac": achieved_tops / peak_tops,
+                     "traffic": None,
+                     "ops_per_launch": evals * OPS_PER_EVAL_WIDE,
+                     "peak_note": f"{sms} SMs x 4 schedulers x 32 lanes x {sm_max_mhz:.0f} MHz (max SM clock)"},
+        "e2e": {"value": e2e_value, "unit": "keys/s", "h2d_bytes_per_step": N_KEYS * 8,
+                "d2h_bytes_per_step": blob_bytes},
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+        "wall_s_timed": wall,
+    }
+    if clocks:
+        line["clocks"] = clocks
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(24000)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

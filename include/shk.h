@@ -1,0 +1,166 @@
+/*
+ * shk.h -- C ABI of the GB300 ShockHash-RS construction library (libshk_gpu.so).
+ *
+ * The library builds minimal perfect hash functions (MPHFs): bijections from a
+ * set of N distinct keys onto [0, N) (paper Sec. 1), with the ShockHash-RS
+ * construction: keys hashed to buckets and split recursively (RecSplit, Sec. 2;
+ * fanouts Sec. 5), each leaf solved by the ShockHash seed search (Sec. 3, Eq.
+ * ShockHash: the smallest seed whose 2-choice graph is a pseudoforest, with the
+ * bit-mask filter of Sec. 3), the orientation bits of all keys stored in one
+ * 1-bit retrieval structure (Sec. 2 Retrieval, Sec. 5).  Every step runs in CUDA
+ * kernels on the calling device; the result is bit-identical to the format
+ * defined by the project (version SHKRS001).
+ *
+ * Conventions
+ *   - Every function returns an shk_status and never aborts.  On failure a
+ *     message is available from shk_last_error() (thread-local, valid until
+ *     the next call on the same thread).
+ *   - Input buffers are borrowed for the duration of the call.  Objects that
+ *     the library returns (shk_mphf) are owned by the caller and released with
+ *     shk_free().
+ *   - "Device" pointers are CUDA global-memory addresses of the current
+ *     device; "host" pointers are ordinary (pageable or pinned) host memory.
+ *   - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  The
+ *     functions enqueue their work on that stream and return after it has
+ *     completed (they synchronise it), except where stated.
+ *   - The current CUDA device at call time is the device that is used.
+ */
+#ifndef SHK_H
+#define SHK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SHK_OK = 0,
+  SHK_EINVAL = 1,     /* bad argument (sizes, limits, null pointers)            */
+  SHK_EDUPKEY = 2,    /* two keys have the same 128-bit fingerprint             */
+  SHK_ENOMEM = 3,     /* a host or device allocation failed                     */
+  SHK_ECUDA = 4,      /* a CUDA call failed; the message names it              */
+  SHK_ESEEDCAP = 5,   /* a seed search reached its cap (never in practice)      */
+  SHK_ETIMEOUT = 6,   /* a bounded device wait gave up                          */
+  SHK_EFORMAT = 7,    /* a serialized MPHF is malformed                         */
+  SHK_ECANCELLED = 8  /* reserved for cancelled requests                        */
+} shk_status;
+
+typedef enum {
+  SHK_KEYS_U64 = 0,   /* data: uint64_t[n_keys]                                 */
+  SHK_KEYS_STR = 1,   /* data: uint8_t bytes; str_offsets: uint64_t[n_keys + 1] */
+  SHK_KEYS_FP128 = 2  /* data: uint64_t[2 * n_keys], (lo, hi) per key, used as   */
+                      /*       the 128-bit fingerprint directly                 */
+} shk_key_kind;
+
+/* A borrowed set of keys.  If on_device is non-zero, data (and str_offsets)
+ * are device pointers, otherwise host pointers. */
+typedef struct {
+  int32_t kind;                 /* shk_key_kind                                */
+  int32_t on_device;            /* 0 = host buffers, 1 = device buffers        */
+  const void* data;
+  const uint64_t* str_offsets;  /* SHK_KEYS_STR only, else NULL                */
+  uint64_t n_keys;
+} shk_keys;
+
+/* Leaf-search scheduling (both give identical results). */
+typedef enum {
+  SHK_SCHED_PERSISTENT = 0,     /* one persistent launch over all leaves, work  */
+                                /* stealing over (leaf, seed-chunk) items       */
+  SHK_SCHED_PER_BUCKET = 1      /* one launch per bucket, one warp per leaf     */
+} shk_sched;
+
+/* Build options.  Zero-initialise and set leaf_size and bucket_size; zero in
+ * any other field selects its default. */
+typedef struct {
+  uint32_t leaf_size;        /* n, 2..64 (leaf bit mask is one 64-bit word)      */
+  uint32_t bucket_size;      /* b, n..4096: expected keys per bucket            */
+  uint32_t shard_buckets;    /* retrieval shard = this many buckets; 0 = 8192/b  */
+  uint32_t eps_num;          /* retrieval overhead eps = eps_num/65536; 0 = 3277 */
+  uint32_t sched;            /* shk_sched                                        */
+  uint32_t seeds_per_lane;   /* leaf kernel: seeds per lane per pass, 0 = tuned  */
+  uint32_t chunk_passes;     /* leaf kernel: passes per work item, 0 = tuned     */
+  uint32_t profile;          /* 1: time each phase with CUDA events              */
+} shk_build_opts;
+
+/* Statistics of the build that produced an MPHF (shk_build_stats). */
+typedef struct {
+  uint64_t n_keys, n_buckets, n_leaves, n_search_leaves, n_split_nodes;
+  uint64_t leaf_seeds_min;      /* sum over leaves of (seed + 1): the seeds a    */
+                                /* sequential search tests                      */
+  uint64_t leaf_seeds_executed; /* seeds the leaf kernel actually evaluated      */
+  uint64_t leaf_key_evals;      /* sum over leaves of (seed + 1) * m             */
+  uint64_t kernel_launches;     /* library kernels launched by the build         */
+  uint64_t size_bits;           /* shk_size_bits                                 */
+  /* phase times in milliseconds (profile = 1), CUDA events on the stream    */
+  double ms_fingerprint, ms_partition, ms_split, ms_leaf, ms_orient, ms_encode,
+      ms_ribbon, ms_total;
+  uint64_t leaf_launches;       /* launches of the leaf-search kernel           */
+} shk_stats;
+
+typedef struct shk_mphf shk_mphf;
+
+/* shk_build -- construct an MPHF over keys (paper Sec. 5, ShockHash-RS).
+ *   keys:   borrowed; host or device buffers (keys->on_device).
+ *   opts:   leaf_size n in [2, 64]; bucket_size b in [n, 4096].
+ *   out:    receives a new object owned by the caller (shk_free).
+ * Errors: SHK_EINVAL (limits, N >= 2^32, a bucket above 8192 keys),
+ * SHK_EDUPKEY, SHK_ENOMEM, SHK_ECUDA, SHK_ESEEDCAP.  The result is resident on
+ * the current device and also serialisable with shk_serialize. */
+shk_status shk_build(const shk_keys* keys, const shk_build_opts* opts, void* cuda_stream,
+                     shk_mphf** out);
+
+/* shk_build_stats -- statistics of the build that produced mphf. */
+shk_status shk_build_stats(const shk_mphf* mphf, shk_stats* out);
+
+/* shk_query -- ranks of keys (paper Sec. 1: x -> p_{g(x)} + h_{g(x)}(x); Sec. 3:
+ * the leaf part is h_{s,f(x)}(x) with f(x) from the retrieval structure).
+ *   ranks_out: uint64_t[keys->n_keys], device memory if out_on_device, else host.
+ * For keys of the build set the ranks are a permutation of [0, N); for other
+ * keys the result is some value in [0, N) (retrieval semantics, Sec. 2). */
+shk_status shk_query(const shk_mphf* mphf, const shk_keys* keys, uint64_t* ranks_out,
+                     int out_on_device, void* cuda_stream);
+
+/* shk_serialize -- copy the encoded MPHF (format SHKRS001) into buf (host).
+ * With buf == NULL or cap too small, only *len is set (and SHK_EINVAL is
+ * returned if buf was given but too small). */
+shk_status shk_serialize(const shk_mphf* mphf, uint8_t* buf, size_t cap, size_t* len);
+
+/* shk_deserialize -- load a serialized MPHF (host bytes) onto the current
+ * device.  SHK_EFORMAT if the bytes are not a well-formed SHKRS001 object. */
+shk_status shk_deserialize(const uint8_t* buf, size_t len, shk_mphf** out);
+
+/* shk_size_bits -- size of the encoded MPHF in bits (header included). */
+uint64_t shk_size_bits(const shk_mphf* mphf);
+
+/* shk_free -- release an MPHF and its device memory.  NULL is ignored. */
+void shk_free(shk_mphf* mphf);
+
+/* shk_last_error -- message of the last failure on this thread ("" if none). */
+const char* shk_last_error(void);
+
+/* shk_leaf_search -- batched ShockHash leaf search over independent leaves
+ * (paper Sec. 3: for each leaf the smallest seed >= seed_start whose graph
+ * ([m], {{h0(x), h1(x)}}) is a pseudoforest, found with the bit-mask filter
+ * and a union-find test of survivors; f = the lexicographically smallest
+ * 1-orientation).
+ *   leaf_keys: device uint64_t[leaf_off[n_leaves]]: the 64-bit leaf inputs x.
+ *   leaf_off:  device uint32_t[n_leaves + 1]; leaf i holds
+ *              leaf_keys[leaf_off[i] .. leaf_off[i+1]), 1 <= size <= 64.
+ *   seeds_out: device uint64_t[n_leaves].
+ *   f_out:     device uint64_t[n_leaves] or NULL; bit j = f of key j.
+ * The persistent launch is captured in a CUDA graph and replayed.  Errors:
+ * SHK_EINVAL (a leaf of size 0 or above 64), SHK_ESEEDCAP, SHK_ECUDA. */
+shk_status shk_leaf_search(const uint64_t* leaf_keys, const uint32_t* leaf_off,
+                           uint32_t n_leaves, uint64_t seed_start, uint64_t* seeds_out,
+                           uint64_t* f_out, void* cuda_stream);
+
+/* shk_version -- format version string ("SHKRS001"). */
+const char* shk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHK_H */

@@ -53,8 +53,8 @@ enum {
 enum { ORC_KEYS_U64 = 0, ORC_KEYS_STR = 1, ORC_KEYS_FP128 = 2 };
 
 #define ORC_MAX_LEAF 64u
-#define ORC_MAX_BUCKET_KEYS 12288u
-#define ORC_MAX_BUCKET_SIZE 8192u
+#define ORC_MAX_BUCKET_KEYS 8192u
+#define ORC_MAX_BUCKET_SIZE 4096u
 #define ORC_SEED_CAP (1ull << 40)
 #define ORC_RIBBON_SEEDS 256u
 #define ORC_HEADER_WORDS 16u
@@ -396,8 +396,8 @@ int orc_leaf_search_batch(const uint64_t* x, const uint32_t* leaf_off, uint32_t 
     int st = ORC_OK;
     if (m == 0 || m > ORC_MAX_LEAF) {
       st = ORC_EINVAL;
-    } else if (m == 1) {
-      s = 0;
+    } else if (m == 1) { /* one key: no hash, any seed works; the first is seed_start */
+      s = seed_start;
       f[0] = 0;
     } else {
       st = orc_leaf_seed(x + leaf_off[i], m, seed_start, ORC_SEED_CAP, 1, &s);

@@ -1,0 +1,267 @@
+"""GB300 ShockHash-RS construction: thin Python binding of libshk_gpu.so.
+
+The functions below carry the names of the C ABI (include/shk.h) and only
+marshal arguments: every step of the construction runs in the library's CUDA
+kernels.  If the library has not been built, or no CUDA device is present,
+every call raises -- there is no CPU fallback.
+
+PyTorch is used for device memory and streams only: tensors are passed to the
+library as raw device pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libshk_gpu.so")
+
+SHK_OK, SHK_EINVAL, SHK_EDUPKEY, SHK_ENOMEM, SHK_ECUDA, SHK_ESEEDCAP, SHK_ETIMEOUT, SHK_EFORMAT = range(8)
+SHK_KEYS_U64, SHK_KEYS_STR, SHK_KEYS_FP128 = 0, 1, 2
+SHK_SCHED_PERSISTENT, SHK_SCHED_PER_BUCKET = 0, 1
+
+# exported symbols declared in include/shk.h
+EXPORTS = ("shk_build", "shk_build_stats", "shk_query", "shk_serialize", "shk_deserialize",
+           "shk_size_bits", "shk_free", "shk_last_error", "shk_leaf_search", "shk_version")
+
+
+class ShkError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"shk error {status}: {message}")
+        self.status = status
+
+
+class _Keys(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("on_device", ctypes.c_int32), ("data", ctypes.c_void_p),
+                ("str_offsets", ctypes.c_void_p), ("n_keys", ctypes.c_uint64)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint32) for name in
+                ("leaf_size", "bucket_size", "shard_buckets", "eps_num", "sched", "seeds_per_lane",
+                 "chunk_passes", "profile")]
+
+
+_STAT_U64 = ["n_keys", "n_buckets", "n_leaves", "n_search_leaves", "n_split_nodes", "leaf_seeds_min",
+             "leaf_seeds_executed", "leaf_key_evals", "kernel_launches", "size_bits"]
+_STAT_F64 = ["ms_fingerprint", "ms_partition", "ms_split", "ms_leaf", "ms_orient", "ms_encode",
+             "ms_ribbon", "ms_total"]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = ([(n, ctypes.c_uint64) for n in _STAT_U64] + [(n, ctypes.c_double) for n in _STAT_F64]
+                + [("leaf_launches", ctypes.c_uint64)])
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libshk_gpu.so; raise if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ShkError(SHK_ECUDA, f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    sig = {
+        "shk_build": (i32, [ctypes.POINTER(_Keys), ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]),
+        "shk_build_stats": (i32, [vp, ctypes.POINTER(_Stats)]),
+        "shk_query": (i32, [vp, ctypes.POINTER(_Keys), vp, i32, vp]),
+        "shk_serialize": (i32, [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+        "shk_deserialize": (i32, [vp, ctypes.c_size_t, ctypes.POINTER(vp)]),
+        "shk_size_bits": (u64, [vp]),
+        "shk_free": (None, [vp]),
+        "shk_last_error": (ctypes.c_char_p, []),
+        "shk_leaf_search": (i32, [vp, vp, u32, u64, vp, vp, vp]),
+        "shk_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def shk_last_error() -> str:
+    return load_library().shk_last_error().decode()
+
+
+def _check(status: int):
+    if status != SHK_OK:
+        raise ShkError(status, shk_last_error())
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_handle(stream) -> int | None:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _as_keys(keys, kind: int, str_offsets=None):
+    """Describe keys (torch tensor on CUDA/CPU or numpy array) for the C ABI.
+    Returns (struct, keepalive)."""
+    torch = _torch()
+    keep = []
+    k = _Keys()
+    k.kind = kind
+    if isinstance(keys, torch.Tensor):
+        t = keys.contiguous()
+        keep.append(t)
+        k.on_device = 1 if t.is_cuda else 0
+        k.data = t.data_ptr() if t.numel() else None
+        nbytes = t.numel() * t.element_size()
+    else:
+        a = np.ascontiguousarray(keys)
+        keep.append(a)
+        k.on_device = 0
+        k.data = a.ctypes.data if a.size else None
+        nbytes = a.nbytes
+    if kind == SHK_KEYS_U64:
+        k.n_keys = nbytes // 8
+    elif kind == SHK_KEYS_FP128:
+        k.n_keys = nbytes // 16
+    else:
+        if isinstance(str_offsets, torch.Tensor):
+            o = str_offsets.contiguous()
+            if bool(o.is_cuda) != bool(k.on_device):
+                raise ValueError("string bytes and offsets must be on the same side")
+            keep.append(o)
+            k.str_offsets = o.data_ptr()
+            k.n_keys = o.numel() - 1
+        else:
+            o = np.ascontiguousarray(str_offsets, dtype=np.uint64)
+            keep.append(o)
+            k.str_offsets = o.ctypes.data
+            k.n_keys = o.size - 1
+    return k, keep
+
+
+@dataclass
+class Mphf:
+    """An MPHF resident on the GPU (owned handle; freed by shk_free / close)."""
+
+    handle: int
+
+    def close(self):
+        if self.handle:
+            shk_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def serialize(self) -> bytes:
+        return shk_serialize(self.handle)
+
+    def size_bits(self) -> int:
+        return shk_size_bits(self.handle)
+
+    def stats(self) -> dict:
+        return shk_build_stats(self.handle)
+
+    def query(self, keys, kind: int = SHK_KEYS_U64, str_offsets=None, out=None, stream=None):
+        return shk_query(self.handle, keys, kind=kind, str_offsets=str_offsets, out=out, stream=stream)
+
+
+def shk_build(keys, leaf_size: int, bucket_size: int, *, kind: int = SHK_KEYS_U64, str_offsets=None,
+              shard_buckets: int = 0, eps_num: int = 0, sched: int = SHK_SCHED_PERSISTENT,
+              seeds_per_lane: int = 0, chunk_passes: int = 0, profile: bool = False,
+              stream=None) -> Mphf:
+    lib = load_library()
+    k, keep = _as_keys(keys, kind, str_offsets)
+    o = _Opts(leaf_size, bucket_size, shard_buckets, eps_num, sched, seeds_per_lane, chunk_passes,
+              1 if profile else 0)
+    out = ctypes.c_void_p()
+    _check(lib.shk_build(ctypes.byref(k), ctypes.byref(o), _stream_handle(stream), ctypes.byref(out)))
+    del keep
+    return Mphf(out.value)
+
+
+def shk_build_stats(handle) -> dict:
+    s = _Stats()
+    _check(load_library().shk_build_stats(handle, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in _Stats._fields_}
+
+
+def shk_query(handle, keys, *, kind: int = SHK_KEYS_U64, str_offsets=None, out=None, stream=None):
+    """Ranks of keys.  Device keys give a device int64 tensor (uint64 bits);
+    host keys give a numpy uint64 array, unless out is given."""
+    torch = _torch()
+    lib = load_library()
+    k, keep = _as_keys(keys, kind, str_offsets)
+    n = int(k.n_keys)
+    if out is None:
+        if k.on_device:
+            out = torch.empty(n, dtype=torch.int64, device=keys.device)
+        else:
+            out = np.empty(n, dtype=np.uint64)
+    if isinstance(out, torch.Tensor):
+        ptr, on_dev = out.data_ptr(), int(out.is_cuda)
+    else:
+        ptr, on_dev = out.ctypes.data, 0
+    _check(lib.shk_query(handle, ctypes.byref(k), ptr if n else None, on_dev, _stream_handle(stream)))
+    del keep
+    return out
+
+
+def shk_serialize(handle) -> bytes:
+    lib = load_library()
+    n = ctypes.c_size_t()
+    _check(lib.shk_serialize(handle, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib.shk_serialize(handle, buf, n.value, ctypes.byref(n)))
+    return buf.raw[: n.value]
+
+
+def shk_deserialize(data: bytes) -> Mphf:
+    lib = load_library()
+    out = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(lib.shk_deserialize(buf, len(data), ctypes.byref(out)))
+    return Mphf(out.value)
+
+
+def shk_size_bits(handle) -> int:
+    return int(load_library().shk_size_bits(handle))
+
+
+def shk_free(handle) -> None:
+    load_library().shk_free(handle)
+
+
+def shk_version() -> str:
+    return load_library().shk_version().decode()
+
+
+def shk_leaf_search(leaf_keys, leaf_off, seed_start: int = 0, want_f: bool = True, stream=None):
+    """Batched leaf search on device tensors: leaf_keys (int64/uint64 bits,
+    the 64-bit leaf inputs), leaf_off (int32, n_leaves + 1 offsets).  Returns
+    (seeds, f_masks) as device int64 tensors (f_masks None if not wanted)."""
+    torch = _torch()
+    lib = load_library()
+    if not (leaf_keys.is_cuda and leaf_off.is_cuda):
+        raise ValueError("shk_leaf_search takes device tensors")
+    kk = leaf_keys.contiguous()
+    off = leaf_off.contiguous()
+    nl = off.numel() - 1
+    seeds = torch.empty(max(nl, 1), dtype=torch.int64, device=kk.device)
+    f = torch.empty(max(nl, 1), dtype=torch.int64, device=kk.device) if want_f else None
+    _check(lib.shk_leaf_search(kk.data_ptr(), off.data_ptr(), nl, seed_start, seeds.data_ptr(),
+                               f.data_ptr() if f is not None else None, _stream_handle(stream)))
+    return seeds[:nl], (f[:nl] if f is not None else None)

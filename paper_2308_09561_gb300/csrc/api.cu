@@ -1,0 +1,529 @@
+// api.cu -- the C ABI (include/shk.h): build, query, (de)serialisation and the
+// batched leaf search.  Host code only orchestrates; every step of the
+// construction runs in the kernels of this library.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace shk {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+shk_status fail(shk_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+shk_status init_ctx(Ctx& c) {
+  SHK_CUDA(cudaGetDevice(&c.device));
+  SHK_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device));
+  return SHK_OK;
+}
+
+static shk_status device_errors(uint32_t e) {
+  if (e & kErrDup) return fail(SHK_EDUPKEY, "two keys have the same 128-bit fingerprint");
+  if (e & kErrBucketOverflow) return fail(SHK_EINVAL, "a bucket holds more than 8192 keys");
+  if (e & kErrLeafSize) return fail(SHK_EINVAL, "a leaf has 0 or more than 64 keys");
+  if (e & kErrSeedCap) return fail(SHK_ESEEDCAP, "a seed search reached 2^40");
+  if (e & kErrRibbon) return fail(SHK_ESEEDCAP, "a retrieval shard was unsolvable for 256 seeds");
+  if (e & kErrOrient) return fail(SHK_ECUDA, "internal: orientation of a leaf failed");
+  return SHK_OK;
+}
+
+// Phase timer on the build stream (profile = 1).
+struct PhaseTimer {
+  bool on;
+  cudaStream_t st;
+  cudaEvent_t ev[12];
+  int n = 0;
+  PhaseTimer(bool enabled, cudaStream_t s) : on(enabled), st(s) {}
+  ~PhaseTimer() {
+    for (int i = 0; i < n; i++) cudaEventDestroy(ev[i]);
+  }
+  int mark() {
+    if (!on || n >= 12) return -1;
+    cudaEventCreate(&ev[n]);
+    cudaEventRecord(ev[n], st);
+    return n++;
+  }
+  double ms(int a, int b) const {
+    if (!on || a < 0 || b < 0) return 0.0;
+    float t = 0;
+    cudaEventElapsedTime(&t, ev[a], ev[b]);
+    return t;
+  }
+};
+
+static uint32_t default_seeds_per_lane(uint32_t n) { return n <= 8 ? 1u : 4u; }
+static uint32_t default_passes(uint32_t n) { return n <= 24 ? 4u : 8u; }
+
+__global__ void k_u64_to_u32(const uint64_t* in, uint64_t n, uint32_t* out) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (uint32_t)in[i];
+}
+
+__global__ void k_leaf_descs(const uint32_t* off, uint32_t n_leaves, LeafDesc* d) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_leaves) return;
+  LeafDesc v;
+  v.key_off = off[i];
+  v.m = off[i + 1] - off[i];
+  v.code_idx = kNoCode;
+  v.bucket = 0;
+  d[i] = v;
+}
+
+template <class T>
+static shk_status d2h(Ctx& c, T* host, const T* dev, size_t count = 1) {
+  SHK_CUDA(cudaMemcpyAsync(host, dev, count * sizeof(T), cudaMemcpyDeviceToHost, c.stream));
+  return SHK_OK;
+}
+
+static void layout(shk_mphf* m) {
+  const uint64_t* h = m->hdr;
+  const uint64_t B = h[4], rice_bits = h[8], lK = h[9], khb = h[10], lO = h[11], ohb = h[12],
+                 rib = h[13], ns = h[7];
+  uint64_t p = kHeaderWords;
+  m->off_rice = p;
+  p += (rice_bits + 63) / 64;
+  m->off_kl = p;
+  p += ((B + 1) * lK + 63) / 64;
+  m->off_kh = p;
+  p += (khb + 63) / 64;
+  m->off_ol = p;
+  p += ((B + 1) * lO + 63) / 64;
+  m->off_oh = p;
+  p += (ohb + 63) / 64;
+  m->off_seed = p;
+  p += (ns + 7) / 8;
+  m->off_rib = p;
+  p += (rib + 63) / 64;
+  m->words = p;
+}
+
+static void free_mphf(shk_mphf* m) {
+  if (!m) return;
+  if (m->d_blob) cudaFree(m->d_blob);
+  if (m->d_K) cudaFree(m->d_K);
+  if (m->d_O) cudaFree(m->d_O);
+  if (m->d_shard_off) cudaFree(m->d_shard_off);
+  delete m;
+}
+
+// Keys to the device (a copy when they are host buffers).
+static shk_status stage_keys(Ctx& c, const shk_keys* keys, const void** data, const uint64_t** offs) {
+  *data = keys->data;
+  *offs = keys->str_offsets;
+  const uint64_t N = keys->n_keys;
+  if (keys->on_device || N == 0) return SHK_OK;
+  if (keys->kind == SHK_KEYS_U64 || keys->kind == SHK_KEYS_FP128) {
+    const size_t bytes = N * (keys->kind == SHK_KEYS_U64 ? 8 : 16);
+    uint8_t* d;
+    SHK_TRY(c.arena.alloc(&d, bytes));
+    SHK_CUDA(cudaMemcpyAsync(d, keys->data, bytes, cudaMemcpyHostToDevice, c.stream));
+    *data = d;
+  } else {
+    const uint64_t total = keys->str_offsets[N];
+    uint8_t* d;
+    uint64_t* o;
+    SHK_TRY(c.arena.alloc(&d, total + 8));
+    SHK_TRY(c.arena.alloc(&o, N + 1));
+    SHK_CUDA(cudaMemcpyAsync(d, keys->data, total, cudaMemcpyHostToDevice, c.stream));
+    SHK_CUDA(cudaMemcpyAsync(o, keys->str_offsets, (N + 1) * 8, cudaMemcpyHostToDevice, c.stream));
+    *data = d;
+    *offs = o;
+  }
+  return SHK_OK;
+}
+
+static shk_status check_keys(const shk_keys* keys) {
+  if (!keys) return fail(SHK_EINVAL, "keys is NULL");
+  if (keys->kind != SHK_KEYS_U64 && keys->kind != SHK_KEYS_STR && keys->kind != SHK_KEYS_FP128)
+    return fail(SHK_EINVAL, "unknown key kind");
+  if (keys->n_keys && !keys->data) return fail(SHK_EINVAL, "key data is NULL");
+  if (keys->kind == SHK_KEYS_STR && keys->n_keys && !keys->str_offsets)
+    return fail(SHK_EINVAL, "string keys need str_offsets");
+  return SHK_OK;
+}
+
+static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cudaStream_t st,
+                             shk_mphf** out) {
+  SHK_TRY(check_keys(keys));
+  const uint64_t N = keys->n_keys;
+  const uint32_t n = o->leaf_size, b = o->bucket_size;
+  if (n < 2 || n > kMaxLeaf) return fail(SHK_EINVAL, "leaf_size must be in [2, 64]");
+  if (b < n || b > kMaxBucketSize) return fail(SHK_EINVAL, "bucket_size must be in [leaf_size, 4096]");
+  if (N >= (1ull << 32)) return fail(SHK_EINVAL, "at most 2^32 - 1 keys");
+  if (o->sched > SHK_SCHED_PER_BUCKET) return fail(SHK_EINVAL, "unknown schedule");
+  const uint32_t S = o->shard_buckets ? o->shard_buckets : std::max(1u, 8192u / b);
+  const uint32_t eps = o->eps_num ? o->eps_num : kDefaultEpsNum;
+  const uint32_t U = o->seeds_per_lane ? o->seeds_per_lane : default_seeds_per_lane(n);
+  const uint32_t passes = o->chunk_passes ? o->chunk_passes : default_passes(n);
+  if (U != 1 && U != 2 && U != 4) return fail(SHK_EINVAL, "seeds_per_lane must be 1, 2 or 4");
+
+  Ctx c(st);
+  SHK_TRY(init_ctx(c));
+  PhaseTimer pt(o->profile != 0, st);
+  const int t0 = pt.mark();
+  const uint64_t B = N ? (N + b - 1) / b : 0;
+  const uint32_t N32 = (uint32_t)N;
+
+  const void* kdata;
+  const uint64_t* koffs;
+  SHK_TRY(stage_keys(c, keys, &kdata, &koffs));
+
+  // a1: fingerprints, buckets, histogram
+  uint64_t *lo, *hi;
+  uint32_t *bkt, *counts, *err;
+  SHK_TRY(c.arena.alloc(&lo, N));
+  SHK_TRY(c.arena.alloc(&hi, N));
+  SHK_TRY(c.arena.alloc(&bkt, N));
+  SHK_TRY(c.arena.alloc(&counts, B, true));
+  SHK_TRY(c.arena.alloc(&err, 1, true));
+  SHK_TRY(launch_fingerprint(c, keys->kind, kdata, koffs, N32, B, lo, hi, bkt, counts));
+  const int t1 = pt.mark();
+
+  // tree shape of every bucket, prefix sums, one host sync for the sizes
+  uint32_t *K, *nleaf, *ncode, *nsplit, *leaf_base, *code_base, *split_base, *maxb;
+  SHK_TRY(c.arena.alloc(&K, B + 1));
+  SHK_TRY((exclusive_scan<uint32_t, uint32_t>(c, counts, B, K)));
+  SHK_TRY(c.arena.alloc(&nleaf, B));
+  SHK_TRY(c.arena.alloc(&ncode, B));
+  SHK_TRY(c.arena.alloc(&nsplit, B));
+  SHK_TRY(c.arena.alloc(&maxb, 1, true));
+  SHK_TRY(launch_tree_count(c, K, B, n, nleaf, ncode, nsplit, maxb));
+  SHK_TRY(c.arena.alloc(&leaf_base, B + 1));
+  SHK_TRY(c.arena.alloc(&code_base, B + 1));
+  SHK_TRY(c.arena.alloc(&split_base, B + 1));
+  SHK_TRY((exclusive_scan<uint32_t, uint32_t>(c, nleaf, B, leaf_base)));
+  SHK_TRY((exclusive_scan<uint32_t, uint32_t>(c, ncode, B, code_base)));
+  SHK_TRY((exclusive_scan<uint32_t, uint32_t>(c, nsplit, B, split_base)));
+  uint32_t h_maxb = 0, h_L = 0, h_C = 0, h_splits = 0, h_err = 0;
+  SHK_TRY(d2h(c, &h_maxb, maxb));
+  SHK_TRY(d2h(c, &h_L, leaf_base + B));
+  SHK_TRY(d2h(c, &h_C, code_base + B));
+  SHK_TRY(d2h(c, &h_splits, split_base + B));
+  std::vector<uint32_t> h_leaf_base;
+  if (o->sched == SHK_SCHED_PER_BUCKET && B) {
+    h_leaf_base.resize(B + 1);
+    SHK_TRY(d2h(c, h_leaf_base.data(), leaf_base, B + 1));
+  }
+  SHK_CUDA(cudaStreamSynchronize(st));
+  if (h_maxb > kMaxBucketKeys) return fail(SHK_EINVAL, "a bucket holds more than 8192 keys");
+
+  // a2: partition and in-bucket sort
+  uint64_t *slo, *shi;
+  SHK_TRY(c.arena.alloc(&slo, N));
+  SHK_TRY(c.arena.alloc(&shi, N));
+  SHK_TRY(launch_partition(c, lo, hi, bkt, N32, B, K, h_maxb, slo, shi, err));
+  const int t2 = pt.mark();
+
+  // a3: splitting trees
+  uint64_t *codes, *llo, *lhi;
+  uint8_t* code_k;
+  LeafDesc* leaves;
+  SHK_TRY(c.arena.alloc(&codes, h_C));
+  SHK_TRY(c.arena.alloc(&code_k, h_C));
+  SHK_TRY(c.arena.alloc(&leaves, h_L));
+  SHK_TRY(c.arena.alloc(&llo, N));
+  SHK_TRY(c.arena.alloc(&lhi, N));
+  SHK_TRY(launch_split(c, slo, shi, K, B, n, h_maxb, code_base, leaf_base, codes, code_k, leaves,
+                       llo, lhi, err));
+  const int t3 = pt.mark();
+
+  // a4 + a5: leaf seeds
+  unsigned long long *best, *counters;
+  SHK_TRY(c.arena.alloc(&best, h_L));
+  SHK_TRY(c.arena.alloc(&counters, 4, true));  // executed, sum(seed+1), sum((seed+1) m)
+  if (h_L) SHK_CUDA(cudaMemsetAsync(best, 0xFF, (size_t)h_L * 8, st));
+  LeafSearchArgs a{leaves, h_L, llo, 0, best, err, counters, U, passes};
+  uint64_t leaf_launches = 0;
+  if (o->sched == SHK_SCHED_PERSISTENT) {
+    SHK_TRY(launch_leaf_persistent(c, a, n));
+    leaf_launches = h_L ? 1 : 0;
+  } else {
+    for (uint64_t i = 0; i < B; i++) {
+      if (h_leaf_base[i + 1] > h_leaf_base[i]) {
+        SHK_TRY(launch_leaf_range(c, a, h_leaf_base[i], h_leaf_base[i + 1], n));
+        leaf_launches++;
+      }
+    }
+  }
+  const int t4 = pt.mark();
+
+  // a6: orientation (also stores leaf seeds into their code slots)
+  uint8_t* f;
+  SHK_TRY(c.arena.alloc(&f, N, true));
+  SHK_TRY(launch_orient(c, leaves, h_L, llo, best, codes, f, nullptr, err));
+  SHK_TRY(launch_leaf_sums(c, leaves, h_L, best, counters + 1));
+  const int t5 = pt.mark();
+
+  // a7 sizes: Rice bits per bucket, shard slots
+  uint64_t *bucket_bits, *O, *slots, *shard_off;
+  SHK_TRY(c.arena.alloc(&bucket_bits, B));
+  SHK_TRY(c.arena.alloc(&O, B + 1));
+  SHK_TRY(launch_rice_bits(c, codes, code_k, code_base, B, bucket_bits));
+  SHK_TRY((exclusive_scan<uint64_t, uint64_t>(c, bucket_bits, B, O)));
+  const uint64_t num_shards = (B + S - 1) / S;
+  uint32_t* max_sk;
+  SHK_TRY(c.arena.alloc(&slots, num_shards));
+  SHK_TRY(c.arena.alloc(&shard_off, num_shards + 1));
+  SHK_TRY(c.arena.alloc(&max_sk, 1, true));
+  SHK_TRY(launch_shard_slots(c, K, B, S, eps, num_shards, slots));
+  SHK_TRY((exclusive_scan<uint64_t, uint64_t>(c, slots, num_shards, shard_off)));
+  SHK_TRY(launch_max_shard_keys(c, K, B, S, num_shards, max_sk));
+  uint64_t h_rice_bits = 0, h_rib_bits = 0;
+  uint32_t h_max_sk = 0;
+  unsigned long long h_cnt[4] = {0, 0, 0, 0};
+  SHK_TRY(d2h(c, &h_rice_bits, O + B));
+  SHK_TRY(d2h(c, &h_rib_bits, shard_off + num_shards));
+  SHK_TRY(d2h(c, &h_max_sk, max_sk));
+  SHK_TRY(d2h(c, h_cnt, counters, 4));
+  SHK_TRY(d2h(c, &h_err, err));
+  SHK_CUDA(cudaStreamSynchronize(st));
+  SHK_TRY(device_errors(h_err));
+
+  // the encoded object
+  shk_mphf* m = new shk_mphf();
+  SHK_CUDA(cudaGetDevice(&m->device));
+  const uint32_t lK = ef_low_bits(N, B + 1), lO = ef_low_bits(h_rice_bits, B + 1);
+  const uint64_t hdr[kHeaderWords] = {kMagic, N, n, b, B, S, eps, num_shards, h_rice_bits, lK,
+                                      (N >> lK) + B + 1, lO, (h_rice_bits >> lO) + B + 1,
+                                      h_rib_bits, 0, 0};
+  memcpy(m->hdr, hdr, sizeof hdr);
+  layout(m);
+  shk_status rs = SHK_OK;
+  auto cuda_ok = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && rs == SHK_OK) rs = fail(SHK_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaSuccess;
+  };
+  if (cuda_ok(cudaMalloc(&m->d_blob, m->words * 8), "cudaMalloc") &&
+      cuda_ok(cudaMalloc(&m->d_K, (B + 1) * 4), "cudaMalloc") &&
+      cuda_ok(cudaMalloc(&m->d_O, (B + 1) * 8), "cudaMalloc") &&
+      cuda_ok(cudaMalloc(&m->d_shard_off, (num_shards + 1) * 8), "cudaMalloc") &&
+      cuda_ok(cudaMemsetAsync(m->d_blob, 0, m->words * 8, st), "cudaMemsetAsync") &&
+      cuda_ok(cudaMemcpyAsync(m->d_blob, hdr, sizeof hdr, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync")) {
+    if (B == 0) {
+      // N = 0: K = O = (0); both Elias-Fano sequences are a single set bit
+      cuda_ok(cudaMemsetAsync(K, 0, 4, st), "cudaMemsetAsync");
+      cuda_ok(cudaMemsetAsync(O, 0, 8, st), "cudaMemsetAsync");
+    }
+    rs = launch_rice_write(c, codes, code_k, code_base, B, O, m->d_blob + m->off_rice);
+    if (rs == SHK_OK) rs = launch_ef_write_u32(c, K, B + 1, lK, m->d_blob + m->off_kl, m->d_blob + m->off_kh);
+    if (rs == SHK_OK) rs = launch_ef_write_u64(c, O, B + 1, lO, m->d_blob + m->off_ol, m->d_blob + m->off_oh);
+  }
+  const int t6 = pt.mark();
+  if (rs == SHK_OK)
+    rs = launch_ribbon(c, llo, lhi, f, K, B, S, eps, num_shards, shard_off,
+                       (uint32_t)shard_slots(h_max_sk, eps), m->d_blob + m->off_rib,
+                       (uint8_t*)(m->d_blob + m->off_seed), err);
+  const int t7 = pt.mark();
+  if (rs == SHK_OK) {
+    cuda_ok(cudaMemcpyAsync(m->d_K, K, (B + 1) * 4, cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync");
+    cuda_ok(cudaMemcpyAsync(m->d_O, O, (B + 1) * 8, cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync");
+    if (num_shards)
+      cuda_ok(cudaMemcpyAsync(m->d_shard_off, shard_off, (num_shards + 1) * 8, cudaMemcpyDeviceToDevice, st),
+              "cudaMemcpyAsync");
+    else
+      cuda_ok(cudaMemsetAsync(m->d_shard_off, 0, 8, st), "cudaMemsetAsync");
+    cuda_ok(cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (rs == SHK_OK) rs = device_errors(h_err);
+  }
+  if (rs != SHK_OK) {
+    cudaStreamSynchronize(st);
+    free_mphf(m);
+    return rs;
+  }
+  shk_stats& s = m->stats;
+  s.n_keys = N;
+  s.n_buckets = B;
+  s.n_leaves = h_L;
+  s.n_search_leaves = h_L;
+  s.n_split_nodes = h_splits;
+  s.leaf_seeds_executed = h_cnt[0];
+  s.leaf_seeds_min = h_cnt[1];
+  s.leaf_key_evals = h_cnt[2];
+  s.kernel_launches = c.launches;
+  s.leaf_launches = leaf_launches;
+  s.size_bits = m->words * 64;
+  s.ms_fingerprint = pt.ms(t0, t1);
+  s.ms_partition = pt.ms(t1, t2);
+  s.ms_split = pt.ms(t2, t3);
+  s.ms_leaf = pt.ms(t3, t4);
+  s.ms_orient = pt.ms(t4, t5);
+  s.ms_encode = pt.ms(t5, t6);
+  s.ms_ribbon = pt.ms(t6, t7);
+  s.ms_total = pt.ms(t0, t7);
+  *out = m;
+  return SHK_OK;
+}
+
+}  // namespace shk
+
+using namespace shk;
+
+extern "C" const char* shk_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* shk_version(void) { return "SHKRS001"; }
+
+extern "C" shk_status shk_build(const shk_keys* keys, const shk_build_opts* opts, void* cuda_stream,
+                                shk_mphf** out) {
+  if (!out || !opts) return fail(SHK_EINVAL, "NULL argument");
+  *out = nullptr;
+  g_last_error.clear();
+  shk_status st = build_impl(keys, opts, (cudaStream_t)cuda_stream, out);
+  if (st != SHK_OK) cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  return st;
+}
+
+extern "C" shk_status shk_build_stats(const shk_mphf* m, shk_stats* out) {
+  if (!m || !out) return fail(SHK_EINVAL, "NULL argument");
+  *out = m->stats;
+  return SHK_OK;
+}
+
+extern "C" uint64_t shk_size_bits(const shk_mphf* m) { return m ? m->words * 64 : 0; }
+
+extern "C" void shk_free(shk_mphf* m) { free_mphf(m); }
+
+extern "C" shk_status shk_serialize(const shk_mphf* m, uint8_t* buf, size_t cap, size_t* len) {
+  if (!m || !len) return fail(SHK_EINVAL, "NULL argument");
+  *len = m->words * 8;
+  if (!buf) return SHK_OK;
+  if (cap < *len) return fail(SHK_EINVAL, "buffer too small");
+  SHK_CUDA(cudaMemcpy(buf, m->d_blob, *len, cudaMemcpyDeviceToHost));
+  return SHK_OK;
+}
+
+extern "C" shk_status shk_deserialize(const uint8_t* buf, size_t len, shk_mphf** out) {
+  if (!buf || !out) return fail(SHK_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (len < kHeaderWords * 8 || len % 8) return fail(SHK_EFORMAT, "bad length");
+  shk_mphf* m = new shk_mphf();
+  memcpy(m->hdr, buf, sizeof m->hdr);
+  const uint64_t* h = m->hdr;
+  const uint64_t N = h[1], n = h[2], b = h[3], B = h[4], S = h[5];
+  bool ok = h[0] == kMagic && n >= 2 && n <= kMaxLeaf && b >= n && b <= kMaxBucketSize &&
+            N < (1ull << 32) && B == (N ? (N + b - 1) / b : 0) && S >= 1 &&
+            h[7] == (B + S - 1) / S && h[9] < 64 && h[11] < 64 && h[9] == ef_low_bits(N, B + 1) &&
+            h[10] == (N >> h[9]) + B + 1 && h[11] == ef_low_bits(h[8], B + 1) &&
+            h[12] == (h[8] >> h[11]) + B + 1 && h[8] < (1ull << 48) && h[13] < (1ull << 48);
+  if (ok) {
+    layout(m);
+    ok = m->words * 8 == len;
+  }
+  if (!ok) {
+    delete m;
+    return fail(SHK_EFORMAT, "not a well-formed SHKRS001 object");
+  }
+  Ctx c(nullptr);
+  shk_status st = init_ctx(c);
+  m->device = c.device;
+  auto run = [&]() -> shk_status {
+    SHK_CUDA(cudaMalloc(&m->d_blob, m->words * 8));
+    SHK_CUDA(cudaMalloc(&m->d_K, (B + 1) * 4));
+    SHK_CUDA(cudaMalloc(&m->d_O, (B + 1) * 8));
+    SHK_CUDA(cudaMalloc(&m->d_shard_off, (h[7] + 1) * 8));
+    SHK_CUDA(cudaMemcpy(m->d_blob, buf, len, cudaMemcpyHostToDevice));
+    uint64_t* K64;
+    SHK_TRY(c.arena.alloc(&K64, B + 1));
+    SHK_TRY(launch_ef_decode(c, m->d_blob + m->off_kl, m->d_blob + m->off_kh, h[10], (uint32_t)h[9],
+                             B + 1, K64));
+    k_u64_to_u32<<<(unsigned)((B + 1 + 255) / 256), 256, 0, c.stream>>>(K64, B + 1, m->d_K);
+    SHK_TRY(launch_ef_decode(c, m->d_blob + m->off_ol, m->d_blob + m->off_oh, h[12], (uint32_t)h[11],
+                             B + 1, m->d_O));
+    uint32_t* bad;
+    uint32_t h_bad = 0;
+    SHK_TRY(c.arena.alloc(&bad, 1, true));
+    SHK_TRY(launch_validate_index(c, m->d_K, m->d_O, B, N, h[8], bad));
+    SHK_CUDA(cudaMemcpyAsync(&h_bad, bad, 4, cudaMemcpyDeviceToHost, c.stream));
+    SHK_CUDA(cudaStreamSynchronize(c.stream));
+    if (h_bad) return fail(SHK_EFORMAT, "inconsistent bucket index");
+    uint64_t* slots;
+    SHK_TRY(c.arena.alloc(&slots, h[7]));
+    SHK_TRY(launch_shard_slots(c, m->d_K, B, (uint32_t)S, (uint32_t)h[6], h[7], slots));
+    SHK_TRY((exclusive_scan<uint64_t, uint64_t>(c, slots, h[7], m->d_shard_off)));
+    SHK_CUDA(cudaStreamSynchronize(c.stream));
+    return SHK_OK;
+  };
+  if (st == SHK_OK) st = run();
+  if (st != SHK_OK) {
+    free_mphf(m);
+    return st;
+  }
+  m->stats.n_keys = N;
+  m->stats.n_buckets = B;
+  m->stats.size_bits = m->words * 64;
+  *out = m;
+  return SHK_OK;
+}
+
+extern "C" shk_status shk_query(const shk_mphf* m, const shk_keys* keys, uint64_t* ranks_out,
+                                int out_on_device, void* cuda_stream) {
+  if (!m || !ranks_out) return fail(SHK_EINVAL, "NULL argument");
+  SHK_TRY(check_keys(keys));
+  const uint64_t nq = keys->n_keys;
+  if (nq && m->hdr[1] == 0) return fail(SHK_EINVAL, "query on an empty MPHF");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Ctx c(st);
+  SHK_TRY(init_ctx(c));
+  auto run = [&]() -> shk_status {
+    const void* kdata;
+    const uint64_t* koffs;
+    SHK_TRY(stage_keys(c, keys, &kdata, &koffs));
+    uint64_t *lo, *hi, *ranks = ranks_out;
+    SHK_TRY(c.arena.alloc(&lo, nq));
+    SHK_TRY(c.arena.alloc(&hi, nq));
+    if (!out_on_device) SHK_TRY(c.arena.alloc(&ranks, nq));
+    SHK_TRY(launch_fingerprint_only(c, keys->kind, kdata, koffs, nq, lo, hi));
+    SHK_TRY(launch_query(c, m, lo, hi, nq, ranks));
+    if (!out_on_device && nq)
+      SHK_CUDA(cudaMemcpyAsync(ranks_out, ranks, nq * 8, cudaMemcpyDeviceToHost, st));
+    SHK_CUDA(cudaStreamSynchronize(st));
+    return SHK_OK;
+  };
+  shk_status s = run();
+  if (s != SHK_OK) cudaStreamSynchronize(st);
+  return s;
+}
+
+extern "C" shk_status shk_leaf_search(const uint64_t* leaf_keys, const uint32_t* leaf_off,
+                                      uint32_t n_leaves, uint64_t seed_start, uint64_t* seeds_out,
+                                      uint64_t* f_out, void* cuda_stream) {
+  if (n_leaves && (!leaf_keys || !leaf_off || !seeds_out)) return fail(SHK_EINVAL, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Ctx c(st);
+  SHK_TRY(init_ctx(c));
+  if (n_leaves == 0) return SHK_OK;
+  auto run = [&]() -> shk_status {
+    LeafDesc* d;
+    uint32_t* err;
+    unsigned long long* counters;
+    SHK_TRY(c.arena.alloc(&d, n_leaves));
+    SHK_TRY(c.arena.alloc(&err, 1, true));
+    SHK_TRY(c.arena.alloc(&counters, 1, true));
+    k_leaf_descs<<<(n_leaves + 255) / 256, 256, 0, st>>>(leaf_off, n_leaves, d);
+    c.launches++;
+    SHK_CUDA(cudaMemsetAsync(seeds_out, 0xFF, (size_t)n_leaves * 8, st));
+    LeafSearchArgs a{d, n_leaves, leaf_keys, seed_start, (unsigned long long*)seeds_out, err,
+                     counters, 4, 8};
+    SHK_TRY(launch_leaf_persistent(c, a, kMaxLeaf));
+    SHK_TRY(launch_orient(c, d, n_leaves, leaf_keys, (unsigned long long*)seeds_out, nullptr,
+                          nullptr, f_out, err));
+    uint32_t h_err = 0;
+    SHK_CUDA(cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, st));
+    SHK_CUDA(cudaStreamSynchronize(st));
+    return device_errors(h_err);
+  };
+  shk_status s = run();
+  if (s != SHK_OK) cudaStreamSynchronize(st);
+  return s;
+}

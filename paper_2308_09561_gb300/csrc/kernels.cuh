@@ -1,0 +1,97 @@
+// kernels.cuh -- launch interfaces of the construction kernels.
+#pragma once
+
+#include "shk_internal.cuh"
+
+namespace shk {
+
+// Per-call context: stream, stream-ordered allocations, device facts and a
+// count of the kernels this call launched.
+struct Ctx {
+  cudaStream_t stream;
+  Arena arena;
+  int num_sms = 0;
+  int device = 0;
+  uint64_t launches = 0;
+  explicit Ctx(cudaStream_t s) : stream(s), arena(s) {}
+};
+
+shk_status init_ctx(Ctx& c);
+
+template <class Tin, class T>
+shk_status exclusive_scan(Ctx& c, const Tin* in, uint64_t n, T* out);
+
+// a1
+shk_status launch_fingerprint(Ctx& c, int kind, const void* data, const uint64_t* offs,
+                              uint32_t n_keys, uint64_t B, uint64_t* lo, uint64_t* hi,
+                              uint32_t* bkt, uint32_t* counts);
+shk_status launch_fingerprint_only(Ctx& c, int kind, const void* data, const uint64_t* offs,
+                                   uint64_t n_keys, uint64_t* lo, uint64_t* hi);
+// a2
+shk_status launch_partition(Ctx& c, const uint64_t* lo, const uint64_t* hi, const uint32_t* bkt,
+                            uint32_t n_keys, uint64_t B, const uint32_t* K, uint32_t max_bucket,
+                            uint64_t* slo, uint64_t* shi, uint32_t* err);
+
+// tree bookkeeping: per bucket the number of searched leaves (m >= 2), of
+// codes (split nodes + searched leaves) and of split nodes; plus the largest
+// bucket (atomicMax into *max_bucket).
+shk_status launch_tree_count(Ctx& c, const uint32_t* K, uint64_t B, uint32_t n,
+                             uint32_t* n_leaves, uint32_t* n_codes, uint32_t* n_splits,
+                             uint32_t* max_bucket);
+// a3
+shk_status launch_split(Ctx& c, const uint64_t* slo, const uint64_t* shi, const uint32_t* K,
+                        uint64_t B, uint32_t n, uint32_t max_bucket, const uint32_t* code_base,
+                        const uint32_t* leaf_base, uint64_t* codes, uint8_t* code_k,
+                        LeafDesc* leaves, uint64_t* llo, uint64_t* lhi, uint32_t* err);
+
+// a4 + a5: leaf seed search.  best[L] must be preset to ~0.
+struct LeafSearchArgs {
+  const LeafDesc* leaves;
+  uint32_t n_leaves;
+  const uint64_t* x;  // leaf inputs, indexed by LeafDesc::key_off
+  uint64_t seed_start;
+  unsigned long long* best;
+  uint32_t* err;
+  unsigned long long* executed;  // seeds evaluated (counter)
+  uint32_t seeds_per_lane;       // 1, 2 or 4
+  uint32_t passes;               // passes per work item
+};
+shk_status launch_leaf_persistent(Ctx& c, const LeafSearchArgs& a, uint32_t max_m);
+shk_status launch_leaf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1,
+                             uint32_t max_m);
+// a6: orientation; writes seeds into codes[code_idx], f per key (leaf order)
+// and optionally f as a mask per leaf.
+shk_status launch_orient(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves, const uint64_t* x,
+                         const unsigned long long* best, uint64_t* codes, uint8_t* f_key,
+                         uint64_t* f_mask, uint32_t* err);
+shk_status launch_leaf_sums(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves,
+                            const unsigned long long* best, unsigned long long* sums);
+
+// a7
+shk_status launch_rice_bits(Ctx& c, const uint64_t* codes, const uint8_t* code_k,
+                            const uint32_t* code_base, uint64_t B, uint64_t* bucket_bits);
+shk_status launch_rice_write(Ctx& c, const uint64_t* codes, const uint8_t* code_k,
+                             const uint32_t* code_base, uint64_t B, const uint64_t* O,
+                             uint64_t* words);
+shk_status launch_ef_write_u32(Ctx& c, const uint32_t* v, uint64_t count, uint32_t l,
+                               uint64_t* low, uint64_t* high);
+shk_status launch_ef_write_u64(Ctx& c, const uint64_t* v, uint64_t count, uint32_t l,
+                               uint64_t* low, uint64_t* high);
+shk_status launch_ef_decode(Ctx& c, const uint64_t* low, const uint64_t* high, uint64_t hbits,
+                            uint32_t l, uint64_t count, uint64_t* out);
+shk_status launch_validate_index(Ctx& c, const uint32_t* K, const uint64_t* O, uint64_t B,
+                                 uint64_t N, uint64_t rice_bits, uint32_t* bad);
+// a8
+shk_status launch_shard_slots(Ctx& c, const uint32_t* K, uint64_t B, uint32_t S, uint32_t eps_num,
+                              uint64_t num_shards, uint64_t* slots);
+shk_status launch_ribbon(Ctx& c, const uint64_t* lo, const uint64_t* hi, const uint8_t* f,
+                         const uint32_t* K, uint64_t B, uint32_t S, uint32_t eps_num,
+                         uint64_t num_shards, const uint64_t* shard_off, uint32_t max_shard_slots,
+                         uint64_t* sol_words, uint8_t* seeds, uint32_t* err);
+shk_status launch_max_shard_keys(Ctx& c, const uint32_t* K, uint64_t B, uint32_t S,
+                                 uint64_t num_shards, uint32_t* out_max);
+// query
+shk_status launch_query(Ctx& c, const shk_mphf* m, const uint64_t* lo, const uint64_t* hi,
+                        uint64_t n, uint64_t* ranks);
+
+}  // namespace shk

@@ -1,0 +1,476 @@
+// leaf.cu -- ShockHash leaf seed search (paper Sec. 3, Eq. ShockHash) with the
+// bit-mask filter (Sec. 3, Filter by Bit Mask), the union-find pseudoforest test
+// of filter survivors (App. A.1) and the orientation of the winning graph
+// (Sec. 4, Eq. orientations-cycles).
+//
+// Warp design: the 32 lanes of a warp test consecutive seeds of one leaf; each
+// lane carries U seeds at once, so every key read from shared memory (a
+// broadcast) feeds U hash evaluations.  A lane keeps each seed's 64-bit
+// candidate mask in two 32-bit registers; a seed survives the filter when the
+// mask has all m bits set.  Survivors (rare) are tested by the whole warp:
+// lanes hash the edges into shared memory and lane 0 runs a union-find with
+// tree/pseudotree labels.  Seeds are taken in increasing order, so the first
+// survivor that passes is the leaf's minimum seed within the work item.
+#include "kernels.cuh"
+
+namespace shk {
+
+constexpr int kLeafThreads = 256;
+constexpr int kLeafWarps = kLeafThreads / 32;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+struct WarpScratch {
+  uint64_t x[kMaxLeaf];
+  uint8_t e0[kMaxLeaf], e1[kMaxLeaf], parent[kMaxLeaf], cyc[kMaxLeaf];
+};
+
+// 1 << h with PTX clamping: shifts of 32 or more give 0.
+__device__ __forceinline__ uint32_t bit32(uint32_t h) {
+  uint32_t r;
+  asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(1u), "r"(h));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t uf_find(uint8_t* parent, uint32_t v) {
+  while (parent[v] != v) {
+    const uint32_t p = parent[v];
+    parent[v] = parent[p];
+    v = parent[p];
+  }
+  return v;
+}
+
+// Union-find pseudoforest test (App. A.1): every set starts as a tree; an edge
+// inside a tree makes it a pseudotree, an edge inside a pseudotree or between
+// two pseudotrees fails.  Run by the whole warp, result in every lane.
+__device__ bool pf_test(WarpScratch* ws, uint32_t m, uint64_t seed) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t c = mix64(kLeafSalt + seed);
+  for (uint32_t i = lane; i < m; i += 32) {
+    uint32_t h0, h1;
+    leaf_cells(ws->x[i], c, m, &h0, &h1);
+    ws->e0[i] = (uint8_t)h0;
+    ws->e1[i] = (uint8_t)h1;
+    ws->parent[i] = (uint8_t)i;
+    ws->cyc[i] = 0;
+  }
+  __syncwarp();
+  int ok = 1;
+  if (lane == 0) {
+    for (uint32_t e = 0; e < m; e++) {
+      const uint32_t a = uf_find(ws->parent, ws->e0[e]);
+      const uint32_t b = uf_find(ws->parent, ws->e1[e]);
+      if (a == b) {
+        if (ws->cyc[a]) {
+          ok = 0;
+          break;
+        }
+        ws->cyc[a] = 1;
+      } else {
+        if (ws->cyc[a] & ws->cyc[b]) {
+          ok = 0;
+          break;
+        }
+        ws->parent[a] = (uint8_t)b;
+        ws->cyc[b] |= ws->cyc[a];
+      }
+    }
+  }
+  ok = __shfl_sync(kFull, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
+
+// Warp-uniform read of a value other warps update.
+__device__ __forceinline__ uint64_t read_uniform(const volatile unsigned long long* p) {
+  unsigned long long v = 0;
+  if ((threadIdx.x & 31) == 0) v = *p;
+  return __shfl_sync(0xFFFFFFFFu, v, 0);
+}
+
+// Search seeds s0 .. s0 + passes*32*U - 1 of the leaf held in ws->x.
+// Returns the smallest passing seed, or ~0 if none (or if *best drops to or
+// below the seeds still to test).  Called by a whole warp; *done counts the
+// seeds evaluated.
+
+template <int U, bool WIDE>
+__device__ uint64_t search_seeds(WarpScratch* ws, uint32_t m, uint64_t s0, uint32_t passes,
+                                 const volatile unsigned long long* best, uint32_t* done) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t full_lo = m >= 32 ? 0xFFFFFFFFu : ((1u << m) - 1u);
+  const uint32_t full_hi = m >= 64 ? 0xFFFFFFFFu : (m > 32 ? ((1u << (m - 32)) - 1u) : 0u);
+  const uint32_t m1 = m - 1;
+  for (uint32_t pass = 0; pass < passes; pass++) {
+    const uint64_t base = s0 + (uint64_t)pass * (32u * U);
+    if (best != nullptr && base >= read_uniform(best)) return ~0ull;
+    *done += 32u * U;
+    uint64_t c[U];
+    uint32_t mlo[U], mhi[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      c[u] = mix64(kLeafSalt + base + (uint64_t)(u * 32) + lane);
+      mlo[u] = 0;
+      mhi[u] = 0;
+    }
+#pragma unroll 2
+    for (uint32_t i = 0; i < m; i++) {
+      const uint64_t x = ws->x[i];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const uint64_t p = (x ^ c[u]) * kLeafMul;
+        const uint32_t h0 = __umulhi((uint32_t)(p >> 32), m);
+        const uint32_t t = __umulhi((uint32_t)p, m1);
+        const uint32_t h1 = t + (t >= h0 ? 1u : 0u);
+        mlo[u] |= bit32(h0) | bit32(h1);
+        if (WIDE) mhi[u] |= bit32(h0 - 32u) | bit32(h1 - 32u);
+      }
+    }
+    bool any = false;
+    bool cov[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      cov[u] = mlo[u] == full_lo && (!WIDE || mhi[u] == full_hi);
+      any |= cov[u];
+    }
+    if (__ballot_sync(kFull, any)) {
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        uint32_t bal = __ballot_sync(kFull, cov[u]);
+        while (bal) {
+          const uint32_t l = __ffs(bal) - 1;
+          const uint64_t s = base + (uint64_t)(u * 32) + l;
+          if (pf_test(ws, m, s)) return s;
+          bal &= bal - 1;
+        }
+      }
+    }
+  }
+  return ~0ull;
+}
+
+template <int U>
+__device__ __forceinline__ uint64_t search_dispatch(WarpScratch* ws, uint32_t m, uint64_t s0,
+                                                    uint32_t passes,
+                                                    const volatile unsigned long long* best,
+                                                    uint32_t* done) {
+  return m > 32 ? search_seeds<U, true>(ws, m, s0, passes, best, done)
+                : search_seeds<U, false>(ws, m, s0, passes, best, done);
+}
+
+__device__ __forceinline__ void load_leaf(WarpScratch* ws, const LeafDesc& d, const uint64_t* x) {
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint32_t i = lane; i < d.m; i += 32) ws->x[i] = x[d.key_off + i];
+  __syncwarp();
+}
+
+// Find a leaf whose result is still open (no passing seed yet).  Each lane
+// reads one word of the closed-leaf bitmap per step.
+__device__ uint32_t find_open_leaf(const uint32_t* closed, uint32_t n_leaves, uint32_t* pos,
+                                   uint32_t salt) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwords = (n_leaves + 31) / 32;
+  const uint32_t tail = n_leaves & 31;
+  for (uint32_t t = 0; t < nwords; t += 32) {
+    const uint32_t wi = (*pos + t + lane) % nwords;
+    uint32_t open = 0;
+    if (t + lane < nwords) {
+      const uint32_t valid = (wi == nwords - 1 && tail) ? ((1u << tail) - 1u) : 0xFFFFFFFFu;
+      open = ~*(const volatile uint32_t*)&closed[wi] & valid;
+    }
+    const uint32_t bal = __ballot_sync(kFull, open != 0);
+    if (bal) {
+      const uint32_t src = __ffs(bal) - 1;
+      uint32_t o = __shfl_sync(kFull, open, src);
+      const uint32_t w = __shfl_sync(kFull, wi, src);
+      *pos = w;
+      // spread helpers over the open leaves of the word
+      uint32_t k = salt % (uint32_t)__popc(o);
+      while (k--) o &= o - 1;
+      return w * 32 + (uint32_t)(__ffs(o) - 1);
+    }
+  }
+  return n_leaves;
+}
+
+// Persistent kernel: every warp takes fresh leaves from a global counter; when
+// none is left it joins leaves that are still open.  Work items are chunks of
+// consecutive seeds of one leaf, handed out in increasing order by a per-leaf
+// counter; a found seed is committed with atomicMin, so the result is the
+// minimum whatever the schedule: every chunk below the final minimum was
+// handed out before the chunk that found it and is searched to its end.
+template <int U>
+__global__ void __launch_bounds__(kLeafThreads)
+    k_leaf_persistent(const LeafDesc* __restrict__ leaves, uint32_t n_leaves,
+                      const uint64_t* __restrict__ x, uint64_t seed_start, uint32_t passes,
+                      unsigned long long* best, uint32_t* next_chunk, uint32_t* closed,
+                      uint32_t* next_leaf, unsigned long long* executed, uint32_t* err) {
+  __shared__ WarpScratch scratch[kLeafWarps];
+  const uint32_t lane = threadIdx.x & 31;
+  WarpScratch* ws = &scratch[threadIdx.x >> 5];
+  const uint32_t gw = blockIdx.x * kLeafWarps + (threadIdx.x >> 5);
+  const uint32_t nwords = (n_leaves + 31) / 32;
+  uint32_t pos = nwords ? (uint32_t)(((uint64_t)gw * 2654435761u) % nwords) : 0;
+  const uint64_t chunk = (uint64_t)passes * 32u * U;
+  unsigned long long done_seeds = 0;
+  for (;;) {
+    uint32_t leaf = 0;
+    if (lane == 0) leaf = atomicAdd(next_leaf, 1u);
+    leaf = __shfl_sync(kFull, leaf, 0);
+    if (leaf >= n_leaves) {
+      leaf = find_open_leaf(closed, n_leaves, &pos, gw);
+      if (leaf >= n_leaves) break;
+    }
+    const LeafDesc d = leaves[leaf];
+    if (d.m < 2 || d.m > kMaxLeaf) {  // a 1-key leaf has no hash: its seed is seed_start
+      if (lane == 0) {
+        if (d.m == 1)
+          best[leaf] = seed_start;
+        else
+          atomicOr(err, kErrLeafSize);
+        atomicOr(&closed[leaf >> 5], 1u << (leaf & 31));
+      }
+      continue;
+    }
+    load_leaf(ws, d, x);
+    for (;;) {
+      uint32_t ci = 0;
+      if (lane == 0) ci = atomicAdd(&next_chunk[leaf], 1u);
+      ci = __shfl_sync(kFull, ci, 0);
+      const uint64_t s0 = seed_start + (uint64_t)ci * chunk;
+      if (s0 >= read_uniform(&best[leaf])) break;
+      if (s0 >= kSeedCap) {
+        if (lane == 0) {
+          atomicOr(err, kErrSeedCap);
+          atomicOr(&closed[leaf >> 5], 1u << (leaf & 31));
+        }
+        break;
+      }
+      uint32_t done = 0;
+      const uint64_t r = search_dispatch<U>(ws, d.m, s0, passes, &best[leaf], &done);
+      done_seeds += done;
+      if (r != ~0ull) {
+        if (lane == 0) {
+          atomicMin(&best[leaf], (unsigned long long)r);
+          atomicOr(&closed[leaf >> 5], 1u << (leaf & 31));
+        }
+        break;
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && done_seeds) atomicAdd(executed, done_seeds);
+}
+
+// One warp per leaf, no sharing: the plain form that is launched once per
+// bucket over that bucket's leaves.
+template <int U>
+__global__ void __launch_bounds__(kLeafThreads)
+    k_leaf_range(const LeafDesc* __restrict__ leaves, uint32_t l0, uint32_t l1,
+                 const uint64_t* __restrict__ x, uint64_t seed_start, uint32_t passes,
+                 unsigned long long* best, unsigned long long* executed, uint32_t* err) {
+  __shared__ WarpScratch scratch[kLeafWarps];
+  const uint32_t lane = threadIdx.x & 31;
+  WarpScratch* ws = &scratch[threadIdx.x >> 5];
+  const uint32_t leaf = l0 + blockIdx.x * kLeafWarps + (threadIdx.x >> 5);
+  if (leaf >= l1) return;
+  const LeafDesc d = leaves[leaf];
+  load_leaf(ws, d, x);
+  const uint64_t chunk = (uint64_t)passes * 32u * U;
+  unsigned long long done_seeds = 0;
+  for (uint64_t s0 = seed_start;; s0 += chunk) {
+    if (s0 >= kSeedCap) {
+      if (lane == 0) atomicOr(err, kErrSeedCap);
+      break;
+    }
+    uint32_t done = 0;
+    const uint64_t r = search_dispatch<U>(ws, d.m, s0, passes, nullptr, &done);
+    done_seeds += done;
+    if (r != ~0ull) {
+      if (lane == 0) best[leaf] = r;
+      break;
+    }
+  }
+  if (lane == 0) atomicAdd(executed, done_seeds);
+}
+
+template <int U>
+static shk_status launch_persistent_u(Ctx& c, const LeafSearchArgs& a) {
+  uint32_t* state;
+  const uint32_t L = a.n_leaves;
+  const uint32_t nwords = (L + 31) / 32;
+  // next_chunk[L] | closed[nwords] | next_leaf[1]
+  SHK_TRY(c.arena.alloc(&state, (size_t)L + nwords + 1, true));
+  int per_sm = 0;
+  SHK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_persistent<U>,
+                                                         kLeafThreads, 0));
+  if (per_sm < 1) per_sm = 1;
+  const uint32_t blocks = (uint32_t)(c.num_sms * per_sm);
+  k_leaf_persistent<U><<<blocks, kLeafThreads, 0, c.stream>>>(
+      a.leaves, L, a.x, a.seed_start, a.passes, a.best, state, state + L, state + L + nwords,
+      a.executed, a.err);
+  c.launches++;
+  SHK_CUDA(cudaGetLastError());
+  return SHK_OK;
+}
+
+shk_status launch_leaf_persistent(Ctx& c, const LeafSearchArgs& a, uint32_t max_m) {
+  (void)max_m;
+  if (a.n_leaves == 0) return SHK_OK;
+  switch (a.seeds_per_lane) {
+    case 1:
+      return launch_persistent_u<1>(c, a);
+    case 2:
+      return launch_persistent_u<2>(c, a);
+    default:
+      return launch_persistent_u<4>(c, a);
+  }
+}
+
+template <int U>
+static shk_status launch_range_u(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1) {
+  const uint32_t blocks = (l1 - l0 + kLeafWarps - 1) / kLeafWarps;
+  k_leaf_range<U><<<blocks, kLeafThreads, 0, c.stream>>>(a.leaves, l0, l1, a.x, a.seed_start,
+                                                         a.passes, a.best, a.executed, a.err);
+  c.launches++;
+  SHK_CUDA(cudaGetLastError());
+  return SHK_OK;
+}
+
+shk_status launch_leaf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1,
+                             uint32_t max_m) {
+  (void)max_m;
+  if (l1 <= l0) return SHK_OK;
+  switch (a.seeds_per_lane) {
+    case 1:
+      return launch_range_u<1>(c, a, l0, l1);
+    case 2:
+      return launch_range_u<2>(c, a, l0, l1);
+    default:
+      return launch_range_u<4>(c, a, l0, l1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a6: orientation.  Tree edges are forced (peel cells of degree one); on each
+// remaining cycle the smallest-index key takes its cell h0 and the cycle is
+// walked from there.  This is the lexicographically smallest f.  One thread per
+// leaf; also stores the leaf's seed into its code slot.
+// ---------------------------------------------------------------------------
+__global__ void k_orient(const LeafDesc* __restrict__ leaves, uint32_t n_leaves,
+                         const uint64_t* __restrict__ x, const unsigned long long* __restrict__ best,
+                         uint64_t* codes, uint8_t* f_key, uint64_t* f_mask, uint32_t* err) {
+  const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n_leaves) return;
+  const LeafDesc d = leaves[l];
+  const uint64_t s = best[l];
+  const uint32_t m = d.m;
+  if (m == 1 && s != ~0ull) {
+    if (f_mask != nullptr) f_mask[l] = 0;
+    return;
+  }
+  if (m < 2 || m > kMaxLeaf || s == ~0ull) {
+    atomicOr(err, kErrOrient);
+    return;
+  }
+  if (codes != nullptr && d.code_idx != kNoCode) codes[d.code_idx] = s;
+  const uint64_t c = mix64(kLeafSalt + s);
+  uint8_t e0[kMaxLeaf], e1[kMaxLeaf], stack[kMaxLeaf];
+  uint64_t inc[kMaxLeaf];
+  for (uint32_t v = 0; v < m; v++) inc[v] = 0;
+  for (uint32_t e = 0; e < m; e++) {
+    uint32_t h0, h1;
+    leaf_cells(x[d.key_off + e], c, m, &h0, &h1);
+    e0[e] = (uint8_t)h0;
+    e1[e] = (uint8_t)h1;
+    inc[h0] |= 1ull << e;
+    inc[h1] |= 1ull << e;
+  }
+  uint64_t live = m == 64 ? ~0ull : ((1ull << m) - 1);
+  uint64_t fb = 0;
+  int sp = 0;
+  for (uint32_t v = 0; v < m; v++)
+    if (__popcll(inc[v]) == 1) stack[sp++] = (uint8_t)v;
+  bool bad = false;
+  while (sp > 0) {
+    const uint32_t v = stack[--sp];
+    const uint64_t em = inc[v] & live;
+    if (em == 0) {  // its last edge was taken from the other side: a tree
+      bad = true;
+      break;
+    }
+    if (__popcll(em) != 1) continue;
+    const uint32_t e = __ffsll((long long)em) - 1;
+    if (e1[e] == v) fb |= 1ull << e;
+    live &= ~(1ull << e);
+    const uint32_t u = e0[e] == v ? e1[e] : e0[e];
+    if (__popcll(inc[u] & live) == 1) stack[sp++] = (uint8_t)u;
+  }
+  while (!bad && live) {
+    const uint32_t e = __ffsll((long long)live) - 1;
+    const uint32_t start = e0[e];
+    live &= ~(1ull << e);  // e takes h0 (f = 0)
+    uint32_t v = e1[e];
+    for (uint32_t guard = 0; v != start; guard++) {
+      const uint64_t em = inc[v] & live;
+      if (em == 0 || guard > m) {
+        bad = true;
+        break;
+      }
+      const uint32_t e2 = __ffsll((long long)em) - 1;
+      if (e1[e2] == v) fb |= 1ull << e2;
+      live &= ~(1ull << e2);
+      v = e0[e2] == v ? e1[e2] : e0[e2];
+    }
+  }
+  if (bad) {
+    atomicOr(err, kErrOrient);
+    return;
+  }
+  if (f_key != nullptr)
+    for (uint32_t e = 0; e < m; e++) f_key[d.key_off + e] = (uint8_t)((fb >> e) & 1);
+  if (f_mask != nullptr) f_mask[l] = fb;
+}
+
+shk_status launch_orient(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves, const uint64_t* x,
+                         const unsigned long long* best, uint64_t* codes, uint8_t* f_key,
+                         uint64_t* f_mask, uint32_t* err) {
+  if (n_leaves == 0) return SHK_OK;
+  k_orient<<<(n_leaves + 127) / 128, 128, 0, c.stream>>>(leaves, n_leaves, x, best, codes, f_key,
+                                                         f_mask, err);
+  c.launches++;
+  SHK_CUDA(cudaGetLastError());
+  return SHK_OK;
+}
+
+// Sums over leaves: sums[0] = sum (seed + 1), sums[1] = sum (seed + 1) * m.
+__global__ void k_leaf_sums(const LeafDesc* leaves, uint32_t n_leaves,
+                            const unsigned long long* best, unsigned long long* sums) {
+  unsigned long long a = 0, b = 0;
+  for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n_leaves;
+       l += gridDim.x * blockDim.x) {
+    const unsigned long long s = best[l] + 1;
+    a += s;
+    b += s * leaves[l].m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(kFull, a, o);
+    b += __shfl_down_sync(kFull, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sums[0], a);
+    atomicAdd(&sums[1], b);
+  }
+}
+
+shk_status launch_leaf_sums(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves,
+                            const unsigned long long* best, unsigned long long* sums) {
+  if (n_leaves == 0) return SHK_OK;
+  uint32_t blocks = (n_leaves + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  k_leaf_sums<<<blocks, 256, 0, c.stream>>>(leaves, n_leaves, best, sums);
+  c.launches++;
+  SHK_CUDA(cudaGetLastError());
+  return SHK_OK;
+}
+
+}  // namespace shk

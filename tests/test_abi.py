@@ -1,0 +1,64 @@
+"""The C-ABI library loads and exports every function include/*.h declares
+(no compute calls: these run without a GPU)."""
+from __future__ import annotations
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(shk_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2308_09561_gb300 import build_ext
+
+    path = build_ext.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ("shk_build", "shk_query", "shk_serialize", "shk_deserialize", "shk_size_bits",
+                 "shk_free", "shk_last_error", "shk_leaf_search", "shk_build_stats"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_the_abi(lib):
+    import paper_2308_09561_gb300 as pkg
+
+    pkg.load_library()
+    for name in _declared():
+        assert callable(getattr(pkg, name)), name
+    assert pkg.shk_version() == "SHKRS001"
+
+
+def test_host_side_argument_errors_without_gpu(lib):
+    """Argument checks happen before any device call."""
+    import paper_2308_09561_gb300 as pkg
+
+    pkg.load_library()
+    with pytest.raises(pkg.ShkError) as e:
+        pkg.shk_deserialize(b"\0" * 64)
+    assert e.value.status in (pkg.SHK_EFORMAT,)
+    with pytest.raises(pkg.ShkError) as e:
+        pkg.shk_deserialize(b"\0" * 130)
+    assert e.value.status == pkg.SHK_EFORMAT

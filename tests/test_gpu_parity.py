@@ -1,0 +1,234 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Builds are compared byte for byte (seeds, Rice and Elias-Fano bits, shard
+seeds, retrieval solution); queries rank for rank.  Small cases span many
+buckets, several tree levels and ragged last leaves; the 10^6-key workload is
+compared on sampled buckets and a sampled retrieval shard, plus the
+bijection over all keys.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import shk_inputs as inp
+from blobfmt import Blob
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+
+    from paper_2308_09561_gb300 import build_ext
+
+    build_ext.build()
+    import paper_2308_09561_gb300 as p
+
+    p.load_library()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return p
+
+
+def _dev(keys):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(keys).view(np.int64)).cuda()
+
+
+def _bijective(ranks_u64, N):
+    return np.array_equal(np.sort(ranks_u64), np.arange(N, dtype=np.uint64))
+
+
+CASES = [(10000, 32, 2000), (3000, 8, 100), (2500, 24, 500), (777, 40, 2000), (1500, 48, 2000),
+         (1, 32, 2000), (2, 2, 2), (129, 16, 16), (4000, 2, 7), (63, 64, 64), (20000, 16, 300),
+         (6000, 12, 4096)]
+
+
+@pytest.mark.parametrize("N,n,b", CASES)
+@pytest.mark.parametrize("sched", [0, 1])
+def test_build_bytes_equal_oracle(pkg, orc, N, n, b, sched):
+    keys = inp.distinct_u64(N, 100 + N)
+    m = pkg.shk_build(_dev(keys), n, b, sched=sched)
+    got = m.serialize()
+    want = orc.build_mphf(keys, n=n, b=b)
+    assert got == want
+    lo, hi = orc.fingerprints_u64(keys)
+    ranks = m.query(_dev(keys)).cpu().numpy().view(np.uint64)
+    assert np.array_equal(ranks, orc.query(want, lo, hi))
+    assert _bijective(ranks, N)
+    st = m.stats()
+    assert st["n_keys"] == N and st["size_bits"] == 8 * len(got)
+    m.close()
+
+
+def test_one_launch_per_bucket_config(pkg, orc):
+    """10,000 keys (stream seed 1), n = 32, b = 2000, one leaf launch per bucket."""
+    keys = inp.distinct_u64(10000, 1)
+    m = pkg.shk_build(_dev(keys), 32, 2000, sched=pkg.SHK_SCHED_PER_BUCKET)
+    st = m.stats()
+    assert st["leaf_launches"] == st["n_buckets"] == 5
+    assert m.serialize() == orc.build_mphf(keys, n=32, b=2000)
+    ranks = m.query(_dev(keys)).cpu().numpy().view(np.uint64)
+    assert _bijective(ranks, 10000)
+
+
+@pytest.mark.parametrize("U,passes", [(1, 1), (2, 3), (4, 16)])
+def test_tuning_knobs_do_not_change_results(pkg, orc, U, passes):
+    keys = inp.distinct_u64(8000, 7)
+    m = pkg.shk_build(_dev(keys), 28, 900, seeds_per_lane=U, chunk_passes=passes)
+    assert m.serialize() == orc.build_mphf(keys, n=28, b=900)
+
+
+def test_host_keys_and_host_ranks(pkg, orc):
+    keys = inp.distinct_u64(5000, 3)
+    m = pkg.shk_build(keys, 20, 600)  # numpy host buffer
+    assert m.serialize() == orc.build_mphf(keys, n=20, b=600)
+    ranks = m.query(keys)  # host in, host out
+    lo, hi = orc.fingerprints_u64(keys)
+    assert np.array_equal(ranks, orc.query(m.serialize(), lo, hi))
+
+
+def test_string_and_fp128_keys(pkg, orc):
+    import torch
+
+    data, offs = inp.ascii_strings(7000, 4)
+    want = orc.build_mphf(kind=orc.KEYS_STR, str_data=data, str_offsets=offs, n=30, b=700)
+    m = pkg.shk_build(torch.from_numpy(data).cuda(), 30, 700, kind=pkg.SHK_KEYS_STR,
+                      str_offsets=torch.from_numpy(offs.view(np.int64)).cuda())
+    assert m.serialize() == want
+    m_host = pkg.shk_build(data, 30, 700, kind=pkg.SHK_KEYS_STR, str_offsets=offs)
+    assert m_host.serialize() == want
+    lo, hi = orc.fingerprints_str(data, offs)
+    fp = np.stack([lo, hi], axis=1).copy()
+    m2 = pkg.shk_build(_dev(fp.reshape(-1)), 30, 700, kind=pkg.SHK_KEYS_FP128)
+    assert m2.serialize() == want
+    r = m.query(torch.from_numpy(data).cuda(), kind=pkg.SHK_KEYS_STR,
+                str_offsets=torch.from_numpy(offs.view(np.int64)).cuda())
+    assert np.array_equal(r.cpu().numpy().view(np.uint64), orc.query(want, lo, hi))
+
+
+def test_empty_and_errors(pkg, orc):
+    import torch
+
+    m = pkg.shk_build(torch.zeros(0, dtype=torch.int64, device="cuda"), 32, 2000)
+    assert m.serialize() == orc.build_mphf(np.zeros(0, np.uint64), n=32, b=2000)
+    keys = inp.distinct_u64(3000, 5)
+    keys[17] = keys[2500]
+    with pytest.raises(pkg.ShkError) as e:
+        pkg.shk_build(_dev(keys), 16, 100)
+    assert e.value.status == pkg.SHK_EDUPKEY
+    for n, b in [(1, 100), (65, 100), (32, 16), (32, 4097)]:
+        with pytest.raises(pkg.ShkError) as e:
+            pkg.shk_build(_dev(inp.distinct_u64(100, 1)), n, b)
+        assert e.value.status == pkg.SHK_EINVAL
+    # the library stays usable after errors
+    k2 = inp.distinct_u64(500, 9)
+    assert pkg.shk_build(_dev(k2), 16, 100).serialize() == orc.build_mphf(k2, n=16, b=100)
+
+
+def test_deserialize_oracle_bytes(pkg, orc):
+    keys = inp.distinct_u64(12000, 11)
+    blob = orc.build_mphf(keys, n=36, b=1500)
+    m = pkg.shk_deserialize(blob)
+    assert m.serialize() == blob
+    lo, hi = orc.fingerprints_u64(keys)
+    ranks = m.query(_dev(keys)).cpu().numpy().view(np.uint64)
+    assert np.array_equal(ranks, orc.query(blob, lo, hi))
+    bad = bytearray(blob)
+    bad[0] ^= 1
+    with pytest.raises(pkg.ShkError) as e:
+        pkg.shk_deserialize(bytes(bad))
+    assert e.value.status == pkg.SHK_EFORMAT
+    with pytest.raises(pkg.ShkError):
+        pkg.shk_deserialize(blob[:-8])
+
+
+def _leaf_case(count, seed, lo_m, hi_m):
+    keys, offs = inp.leaf_instances(count, seed, lo_m, hi_m)
+    return keys, offs
+
+
+@pytest.mark.parametrize("count,seed,lo_m,hi_m,start", [(3000, 3, 1, 40, 0), (500, 5, 2, 44, 12345),
+                                                        (64, 6, 33, 33, 2**33), (40, 8, 45, 50, 0)])
+def test_leaf_search_equals_oracle(pkg, orc, count, seed, lo_m, hi_m, start):
+    import torch
+
+    keys, offs = _leaf_case(count, seed, lo_m, hi_m)
+    want_s, want_f = orc.leaf_search_batch(keys, offs, start)
+    s, f = pkg.shk_leaf_search(_dev(keys), torch.from_numpy(offs.view(np.int32)).cuda(), start)
+    assert np.array_equal(s.cpu().numpy().view(np.uint64), want_s)
+    assert np.array_equal(f.cpu().numpy().view(np.uint64), want_f)
+
+
+def test_leaf_search_largest_leaves(pkg, orc):
+    """Leaves of 56..64 keys (seed searches of ~10^7 seeds each)."""
+    import torch
+
+    keys, offs = _leaf_case(12, 33, 56, 64)
+    want_s, want_f = orc.leaf_search_batch(keys, offs, 0)
+    s, f = pkg.shk_leaf_search(_dev(keys), torch.from_numpy(offs.view(np.int32)).cuda(), 0)
+    assert np.array_equal(s.cpu().numpy().view(np.uint64), want_s)
+    assert np.array_equal(f.cpu().numpy().view(np.uint64), want_f)
+
+
+def test_leaf_search_rejects_bad_sizes(pkg):
+    import torch
+
+    keys = _dev(inp.splitmix64_stream(1, 200))
+    off = torch.tensor([0, 10, 10, 20], dtype=torch.int32, device="cuda")
+    with pytest.raises(pkg.ShkError) as e:
+        pkg.shk_leaf_search(keys, off)
+    assert e.value.status == pkg.SHK_EINVAL
+    off = torch.tensor([0, 65, 70], dtype=torch.int32, device="cuda")
+    with pytest.raises(pkg.ShkError) as e:
+        pkg.shk_leaf_search(keys, off)
+    assert e.value.status == pkg.SHK_EINVAL
+
+
+def test_million_keys_leaf48_sampled(pkg, orc):
+    """10^6 keys (stream seed 2), n = 48, b = 2000, persistent schedule:
+    every key ranks bijectively; sampled buckets' codes and one retrieval
+    shard equal the oracle's; the oracle's decoder reads the GPU bytes."""
+    import torch
+
+    N, n, b = 1_000_000, 48, 2000
+    keys = inp.distinct_u64(N, 2)
+    dk = _dev(keys)
+    m = pkg.shk_build(dk, n, b)
+    blob = m.serialize()
+    ranks = m.query(dk)
+    srt, _ = torch.sort(ranks)
+    assert torch.equal(srt, torch.arange(N, device="cuda", dtype=torch.int64))
+    bl = Blob(blob)
+    assert bl.total_words == bl.nwords
+    B = bl.h["B"]
+    K = bl.K()
+    O = bl.O()
+    lo, hi = orc.fingerprints_u64(keys)
+    bkt = (hi.astype(object) * B) >> 64
+    bkt = np.array(bkt, dtype=np.int64)
+    order = np.lexsort((lo, hi))
+    assert np.array_equal(np.bincount(bkt, minlength=B), np.diff(K.astype(np.int64)))
+    for i in (0, 1, 2, 3, 137, B - 1):
+        sel = order[K[i]:K[i + 1]]
+        seeds, ks, llo, lhi, f = orc.bucket_build(lo[sel], hi[sel], n)
+        codes, end = bl.rice_codes(int(O[i]), [int(k) for k in ks])
+        assert codes == [int(s) for s in seeds]
+        assert end == O[i + 1]
+        if i == 3:  # shard 0 = buckets 0..3
+            S = bl.h["shard_buckets"]
+            assert S == 4
+            parts = [orc.bucket_build(lo[order[K[j]:K[j + 1]]], hi[order[K[j]:K[j + 1]]], n) for j in range(S)]
+            slo = np.concatenate([p[2] for p in parts])
+            shi = np.concatenate([p[3] for p in parts])
+            sf = np.concatenate([p[4] for p in parts])
+            seed, sol = orc.ribbon_shard(slo, shi, sf, bl.h["eps_num"])
+            assert seed == bl.shard_seeds[0]
+            got = [Blob.bit(bl.ribbon, p) for p in range(sol.size)]
+            assert got == [int(v) for v in sol]
+    samp = np.arange(0, N, 37)
+    r_or = orc.query(blob, lo[samp], hi[samp])
+    assert np.array_equal(r_or, ranks.cpu().numpy().view(np.uint64)[samp])
+    m.close()
