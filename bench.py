@@ -153,6 +153,8 @@ def run_reference(args):
 def run_ours(args):
     import torch
 
+    global N_KEYS
+    N_KEYS = args.keys
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     dist = None
@@ -269,6 +271,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--keys", type=int, default=N_KEYS, help="smaller key counts for profiling runs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

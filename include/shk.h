@@ -156,6 +156,24 @@ shk_status shk_leaf_search(const uint64_t* leaf_keys, const uint32_t* leaf_off,
                            uint32_t n_leaves, uint64_t seed_start, uint64_t* seeds_out,
                            uint64_t* f_out, void* cuda_stream);
 
+/* shk_leaf_search_noalloc -- shk_leaf_search without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they run -- a process whose GPU memory
+ * is owned by another memory manager, or a serving loop with a fixed memory
+ * budget that must not meet an out-of-memory error or the device-wide
+ * synchronisation of cudaMalloc/cudaFree mid-request.  Arguments, results and
+ * errors are those of shk_leaf_search; the caller still provides every input
+ * and output buffer.  Working memory comes from one fixed array in the
+ * library's device image (about 1.3 MB, held by every GPU that loads the
+ * library until the process exits), so n_leaves is limited to 65536
+ * (SHK_EINVAL beyond, with a message).  The first call on a device looks up
+ * the array's device address; make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race and
+ * must be serialised by the caller. */
+shk_status shk_leaf_search_noalloc(const uint64_t* leaf_keys, const uint32_t* leaf_off,
+                                   uint32_t n_leaves, uint64_t seed_start, uint64_t* seeds_out,
+                                   uint64_t* f_out, void* cuda_stream);
+
 /* shk_version -- format version string ("SHKRS001"). */
 const char* shk_version(void);
 

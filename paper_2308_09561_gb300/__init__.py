@@ -25,7 +25,8 @@ SHK_SCHED_PERSISTENT, SHK_SCHED_PER_BUCKET = 0, 1
 
 # exported symbols declared in include/shk.h
 EXPORTS = ("shk_build", "shk_build_stats", "shk_query", "shk_serialize", "shk_deserialize",
-           "shk_size_bits", "shk_free", "shk_last_error", "shk_leaf_search", "shk_version")
+           "shk_size_bits", "shk_free", "shk_last_error", "shk_leaf_search", "shk_leaf_search_noalloc",
+           "shk_version")
 
 
 class ShkError(RuntimeError):
@@ -78,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "shk_free": (None, [vp]),
         "shk_last_error": (ctypes.c_char_p, []),
         "shk_leaf_search": (i32, [vp, vp, u32, u64, vp, vp, vp]),
+        "shk_leaf_search_noalloc": (i32, [vp, vp, u32, u64, vp, vp, vp]),
         "shk_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -265,3 +267,20 @@ def shk_leaf_search(leaf_keys, leaf_off, seed_start: int = 0, want_f: bool = Tru
     _check(lib.shk_leaf_search(kk.data_ptr(), off.data_ptr(), nl, seed_start, seeds.data_ptr(),
                                f.data_ptr() if f is not None else None, _stream_handle(stream)))
     return seeds[:nl], (f[:nl] if f is not None else None)
+
+
+def shk_leaf_search_noalloc(leaf_keys, leaf_off, seeds_out, f_out=None, seed_start: int = 0, stream=None):
+    """shk_leaf_search for callers that cannot allocate device memory while
+    they run: the caller passes the output tensors (seeds_out, and f_out or
+    None; int64 device tensors of n_leaves elements) and the library takes its
+    working memory from a fixed array in its device image, so at most 65536
+    leaves per call.  Calls that overlap on the GPU race on that array."""
+    lib = load_library()
+    for t in (leaf_keys, leaf_off, seeds_out) + ((f_out,) if f_out is not None else ()):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("shk_leaf_search_noalloc takes contiguous device tensors")
+    nl = leaf_off.numel() - 1
+    _check(lib.shk_leaf_search_noalloc(leaf_keys.data_ptr(), leaf_off.data_ptr(), nl, seed_start,
+                                       seeds_out.data_ptr(), f_out.data_ptr() if f_out is not None else None,
+                                       _stream_handle(stream)))
+    return seeds_out, f_out

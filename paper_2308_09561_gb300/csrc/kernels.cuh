@@ -57,6 +57,9 @@ struct LeafSearchArgs {
   uint32_t passes;               // passes per work item
 };
 shk_status launch_leaf_persistent(Ctx& c, const LeafSearchArgs& a, uint32_t max_m);
+// As launch_leaf_persistent, with caller-owned state of
+// (n_leaves + (n_leaves + 31) / 32 + 1) u32 words (cleared by the launch).
+shk_status launch_leaf_persistent_state(Ctx& c, const LeafSearchArgs& a, uint32_t* state);
 shk_status launch_leaf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1,
                              uint32_t max_m);
 // a6: orientation; writes seeds into codes[code_idx], f per key (leaf order)

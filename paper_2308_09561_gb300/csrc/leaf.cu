@@ -326,6 +326,38 @@ shk_status launch_leaf_persistent(Ctx& c, const LeafSearchArgs& a, uint32_t max_
   }
 }
 
+// Same launch with the work-distribution state supplied by the caller:
+// state = next_chunk[L] | closed[(L + 31) / 32] | next_leaf[1], zeroed here.
+template <int U>
+static shk_status launch_persistent_state_u(Ctx& c, const LeafSearchArgs& a, uint32_t* state) {
+  const uint32_t L = a.n_leaves;
+  const uint32_t nwords = (L + 31) / 32;
+  SHK_CUDA(cudaMemsetAsync(state, 0, ((size_t)L + nwords + 1) * sizeof(uint32_t), c.stream));
+  int per_sm = 0;
+  SHK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_persistent<U>,
+                                                         kLeafThreads, 0));
+  if (per_sm < 1) per_sm = 1;
+  const uint32_t blocks = (uint32_t)(c.num_sms * per_sm);
+  k_leaf_persistent<U><<<blocks, kLeafThreads, 0, c.stream>>>(
+      a.leaves, L, a.x, a.seed_start, a.passes, a.best, state, state + L, state + L + nwords,
+      a.executed, a.err);
+  c.launches++;
+  SHK_CUDA(cudaGetLastError());
+  return SHK_OK;
+}
+
+shk_status launch_leaf_persistent_state(Ctx& c, const LeafSearchArgs& a, uint32_t* state) {
+  if (a.n_leaves == 0) return SHK_OK;
+  switch (a.seeds_per_lane) {
+    case 1:
+      return launch_persistent_state_u<1>(c, a, state);
+    case 2:
+      return launch_persistent_state_u<2>(c, a, state);
+    default:
+      return launch_persistent_state_u<4>(c, a, state);
+  }
+}
+
 template <int U>
 static shk_status launch_range_u(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1) {
   const uint32_t blocks = (l1 - l0 + kLeafWarps - 1) / kLeafWarps;
