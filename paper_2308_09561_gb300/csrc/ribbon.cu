@@ -49,6 +49,13 @@ shk_status launch_max_shard_keys(Ctx& c, const uint32_t* K, uint64_t B, uint32_t
   return SHK_OK;
 }
 
+// Shared memory of one shard with row precomputation: rows[m] u64 |
+// coefficients[keys] u64 | starts[keys] u32 | rhs[m] u8 | bits[keys] u8.
+__host__ __device__ inline size_t ribbon_smem(uint64_t m, uint64_t keys, bool pre) {
+  return pre ? (size_t)m * 9 + (size_t)keys * 13 + 16 : (size_t)m * 9 + 16;
+}
+
+template <bool PRE>
 __global__ void __launch_bounds__(kRibbonThreads)
     k_ribbon(const uint64_t* __restrict__ lo, const uint64_t* __restrict__ hi,
              const uint8_t* __restrict__ f, const uint32_t* __restrict__ K, uint64_t B, uint32_t S,
@@ -63,7 +70,10 @@ __global__ void __launch_bounds__(kRibbonThreads)
     if (threadIdx.x == 0) seeds[sh] = 0;
     return;
   }
-  uint8_t* rhs = (uint8_t*)(rows + m);
+  uint64_t* pcoef = rows + m;
+  uint32_t* pstart = (uint32_t*)(pcoef + (PRE ? keys : 0));
+  uint8_t* rhs = PRE ? (uint8_t*)(pstart + keys) : (uint8_t*)(rows + m);
+  uint8_t* pbit = rhs + m;
   __shared__ int ok_s;
   __shared__ uint32_t seed_s;
   for (uint32_t r = 0; r < kRibbonSeeds; r++) {
@@ -71,13 +81,29 @@ __global__ void __launch_bounds__(kRibbonThreads)
       rows[i] = 0;
       rhs[i] = 0;
     }
+    if (PRE) {
+      for (uint32_t i = threadIdx.x; i < keys; i += kRibbonThreads) {
+        uint64_t st, cf;
+        ribbon_row(lo[k0 + i], hi[k0 + i], r, m, &st, &cf);
+        pcoef[i] = cf;
+        pstart[i] = (uint32_t)st;
+        pbit[i] = f[k0 + i];
+      }
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       int ok = 1;
       for (uint32_t i = 0; i < keys && ok; i++) {
         uint64_t st, cf;
-        ribbon_row(lo[k0 + i], hi[k0 + i], r, m, &st, &cf);
-        uint8_t bv = f[k0 + i];
+        uint8_t bv;
+        if (PRE) {
+          st = pstart[i];
+          cf = pcoef[i];
+          bv = pbit[i];
+        } else {
+          ribbon_row(lo[k0 + i], hi[k0 + i], r, m, &st, &cf);
+          bv = f[k0 + i];
+        }
         for (;;) {
           const uint64_t row = rows[st];
           if (row == 0) {
@@ -141,11 +167,20 @@ shk_status launch_ribbon(Ctx& c, const uint64_t* lo, const uint64_t* hi, const u
                          uint64_t num_shards, const uint64_t* shard_off, uint32_t max_shard_slots,
                          uint64_t* sol_words, uint8_t* seeds, uint32_t* err) {
   if (num_shards == 0) return SHK_OK;
-  const size_t smem = (size_t)max_shard_slots * 9 + 16;
-  if (smem > 227 * 1024) return fail(SHK_EINVAL, "retrieval shard too large for shared memory");
-  SHK_CUDA(cudaFuncSetAttribute(k_ribbon, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_ribbon<<<(unsigned)num_shards, kRibbonThreads, smem, c.stream>>>(lo, hi, f, K, B, S, eps_num,
-                                                                     shard_off, sol_words, seeds, err);
+  const size_t limit = 227 * 1024;
+  // max_shard_slots belongs to the largest shard, so it bounds its keys too
+  const size_t smem_pre = ribbon_smem(max_shard_slots, max_shard_slots, true);
+  const size_t smem = ribbon_smem(max_shard_slots, 0, false);
+  if (smem_pre <= limit) {
+    SHK_CUDA(cudaFuncSetAttribute(k_ribbon<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pre));
+    k_ribbon<true><<<(unsigned)num_shards, kRibbonThreads, smem_pre, c.stream>>>(
+        lo, hi, f, K, B, S, eps_num, shard_off, sol_words, seeds, err);
+  } else {
+    if (smem > limit) return fail(SHK_EINVAL, "retrieval shard too large for shared memory");
+    SHK_CUDA(cudaFuncSetAttribute(k_ribbon<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_ribbon<false><<<(unsigned)num_shards, kRibbonThreads, smem, c.stream>>>(
+        lo, hi, f, K, B, S, eps_num, shard_off, sol_words, seeds, err);
+  }
   c.launches++;
   SHK_CUDA(cudaGetLastError());
   return SHK_OK;
