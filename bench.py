@@ -105,6 +105,23 @@ def _dist():
     return ws, rank, local
 
 
+def rank_key_seed(rank: int) -> int:
+    """Each rank builds its own independent key set (weak scaling)."""
+    return KEY_SEED + 1000 * rank
+
+
+def max_over_ranks(seconds: float, dist, device) -> float:
+    """The job's time is the slowest rank's time (no data-path collective:
+    only this scalar is reduced)."""
+    if dist is None:
+        return seconds
+    import torch
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _cpu_baseline(sample_keys: int, reps: int = 1):
     """The oracle as it stands on the host cores, on the first sample_keys keys
     of the same stream (same leaf and bucket size)."""
@@ -166,7 +183,7 @@ def run_ours(args):
     import shk_inputs
 
     pkg.load_library()
-    keys = shk_inputs.distinct_u64(N_KEYS, KEY_SEED + 1000 * rank)
+    keys = shk_inputs.distinct_u64(N_KEYS, rank_key_seed(rank))
     dkeys = torch.from_numpy(keys.view(np.int64)).cuda()
     host_keys = torch.from_numpy(keys.view(np.int64)).pin_memory()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # 256 MB > L2
@@ -199,11 +216,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_sum = sum(step_ms) / 1e3
-    if dist:
-        tt = torch.tensor([t_sum], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_sum = float(tt.item())
+    t_sum = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
     value = N_KEYS * ws * args.steps / t_sum
 
     # end to end through the public API: pinned host keys in, serialized MPHF out
@@ -228,6 +241,21 @@ def run_ours(args):
     peak_tops = sms * 4 * 32 * sm_max_mhz * 1e6 / 1e12
     achieved_tops = evals * OPS_PER_EVAL_WIDE / (leaf_ms / 1e3) / 1e12
     clocks = clk.summary()
+    # the plain form: one leaf-search launch per bucket, one warp per leaf, on a
+    # prefix of the same keys (the whole workload with --compare-per-bucket)
+    cmp_keys = N_KEYS if args.compare_per_bucket else min(N_KEYS, 100_000)
+    ck = dkeys[:cmp_keys]
+    t_cmp = {}
+    for name, sched in (("persistent", pkg.SHK_SCHED_PERSISTENT), ("per_bucket", pkg.SHK_SCHED_PER_BUCKET)):
+        m = pkg.shk_build(ck, LEAF, BUCKET, sched=sched, profile=True)
+        st = m.stats()
+        t_cmp[name] = st
+        m.close()
+    per_bucket = {"keys": cmp_keys, "persistent_ms_leaf": t_cmp["persistent"]["ms_leaf"],
+                  "per_bucket_ms_leaf": t_cmp["per_bucket"]["ms_leaf"],
+                  "per_bucket_leaf_launches": t_cmp["per_bucket"]["leaf_launches"],
+                  "speedup_leaf": t_cmp["per_bucket"]["ms_leaf"] / t_cmp["persistent"]["ms_leaf"],
+                  "speedup_build": t_cmp["per_bucket"]["ms_total"] / t_cmp["persistent"]["ms_total"]}
     line = {
         "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_sum / args.steps, "higher_is_better": True,
@@ -251,6 +279,8 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "keys/s", "h2d_bytes_per_step": N_KEYS * 8,
                 "d2h_bytes_per_step": blob_bytes},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+        "leaf_kernel_cfg": stats[-1]["leaf_cfg"],
+        "persistent_vs_per_bucket": per_bucket,
         "wall_s_timed": wall,
     }
     if clocks:
@@ -264,6 +294,63 @@ def run_ours(args):
     return 0
 
 
+def run_leafbatch(args):
+    """65,536 independent leaves, sizes uniform in [40, 64], uniform 64-bit
+    keys (stream seed 3), seed start 0: one graph-captured persistent launch
+    per step (replayed), first passing seed and orientation per leaf."""
+    import torch
+
+    import paper_2308_09561_gb300 as pkg
+    import shk_inputs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pkg.load_library()
+    count = 65536 if args.keys == N_KEYS else args.keys
+    keys, offs = shk_inputs.leaf_instances(count, 3 + 1000 * rank)
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    off = torch.from_numpy(offs.view(np.int32)).cuda()
+    seeds = torch.empty(count, dtype=torch.int64, device="cuda")
+    fm = torch.empty(count, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 0)):
+        pkg.shk_leaf_search(dk, off, 0, seeds_out=seeds, f_out=fm)
+    torch.cuda.synchronize()
+    r0 = pkg.shk_leaf_graph_replays()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            pkg.shk_leaf_search(dk, off, 0, seeds_out=seeds, f_out=fm)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    s = seeds.cpu().numpy().view(np.uint64).astype(np.float64)
+    sizes = np.diff(offs.astype(np.int64))
+    seeds_min = float((s + 1).sum())
+    evals = float(((s + 1) * sizes).sum())
+    peaks = _peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = sms * 4 * 32 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    ach = evals * OPS_PER_EVAL_WIDE / (t / args.steps) / 1e12
+    line = {"metric": "batched leaf search: leaf seeds tested/s (65,536 leaves, m in [40,64])",
+            "value": seeds_min * args.steps / t, "unit": "seeds/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "leaf_batch_65536_leaves_m40_64", "leaves": count, "seed_stream": 3},
+            "key_seed_evals_per_s": evals * args.steps / t, "mean_seed": float(s.mean()),
+            "graph_replays": pkg.shk_leaf_graph_replays() - r0,
+            "tuned_cfg": pkg.shk_leaf_tune(64),
+            "roofline": {"bound": "alu", "kernel": "k_leaf_persistent", "achieved": ach, "peak": peak,
+                         "unit": "T int-lane-ops/s", "frac": ach / peak}}
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -272,9 +359,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--keys", type=int, default=N_KEYS, help="smaller key counts for profiling runs")
+    ap.add_argument("--compare-per-bucket", action="store_true",
+                    help="time the one-launch-per-bucket form on the whole workload (slow)")
+    ap.add_argument("--workload", default="build", choices=["build", "leafbatch"],
+                    help="leafbatch: 65,536 independent leaves of 40..64 keys, one graph-replayed launch")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "leafbatch":
+        return run_leafbatch(args)
     return run_ours(args)
 
 

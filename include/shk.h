@@ -79,9 +79,12 @@ typedef struct {
   uint32_t shard_buckets;    /* retrieval shard = this many buckets; 0 = 8192/b  */
   uint32_t eps_num;          /* retrieval overhead eps = eps_num/65536; 0 = 3277 */
   uint32_t sched;            /* shk_sched                                        */
-  uint32_t seeds_per_lane;   /* leaf kernel: seeds per lane per pass, 0 = tuned  */
-  uint32_t chunk_passes;     /* leaf kernel: passes per work item, 0 = tuned     */
+  uint32_t seeds_per_lane;   /* leaf kernel: seeds per lane per pass (1, 2, 4);  */
+                             /* 0 = the autotuner's choice for this leaf size     */
+  uint32_t chunk_passes;     /* leaf kernel: passes per work item, 0 = default    */
   uint32_t profile;          /* 1: time each phase with CUDA events              */
+  uint32_t warps_per_block;  /* with seeds_per_lane != 0: 4, 8 or 16; 0 = 8      */
+  uint32_t key_unroll;       /* with seeds_per_lane != 0: 1, 2 or 4; 0 = 2       */
 } shk_build_opts;
 
 /* Statistics of the build that produced an MPHF (shk_build_stats). */
@@ -97,6 +100,8 @@ typedef struct {
   double ms_fingerprint, ms_partition, ms_split, ms_leaf, ms_orient, ms_encode,
       ms_ribbon, ms_total;
   uint64_t leaf_launches;       /* launches of the leaf-search kernel           */
+  uint32_t leaf_cfg[4];         /* seeds per lane, warps per block, key unroll,  */
+                                /* passes per work item of the leaf kernel      */
 } shk_stats;
 
 typedef struct shk_mphf shk_mphf;
@@ -173,6 +178,25 @@ shk_status shk_leaf_search(const uint64_t* leaf_keys, const uint32_t* leaf_off,
 shk_status shk_leaf_search_noalloc(const uint64_t* leaf_keys, const uint32_t* leaf_off,
                                    uint32_t n_leaves, uint64_t seed_start, uint64_t* seeds_out,
                                    uint64_t* f_out, void* cuda_stream);
+
+/* shk_leaf_tune -- the leaf kernel configuration the autotuner picks for
+ * leaves of leaf_size keys on the current device (timed once per device and
+ * leaf-size bin, then cached).  cfg_out[4] = seeds per lane, warps per
+ * block, key-loop unroll, passes per work item; evals_per_s (nullable) = its
+ * measured key-seed evaluations per second.  With probe_all, every supported
+ * configuration is timed into all_evals_per_s[shk_leaf_configs()].  The
+ * configuration never changes results. */
+shk_status shk_leaf_tune(uint32_t leaf_size, uint32_t* cfg_out, double* evals_per_s,
+                         int probe_all, double* all_evals_per_s);
+
+/* shk_leaf_configs -- the supported leaf kernel configurations, 4 words each
+ * (as in shk_leaf_tune; passes 0); returns their number. */
+uint32_t shk_leaf_configs(uint32_t* cfgs, uint32_t cap);
+
+/* shk_leaf_graph_replays -- how many times this host thread has launched the
+ * captured leaf-search graph (each shk_leaf_search call launches it once;
+ * calls with unchanged pointers and sizes reuse the instantiated graph). */
+uint64_t shk_leaf_graph_replays(void);
 
 /* shk_version -- format version string ("SHKRS001"). */
 const char* shk_version(void);

@@ -26,7 +26,7 @@ SHK_SCHED_PERSISTENT, SHK_SCHED_PER_BUCKET = 0, 1
 # exported symbols declared in include/shk.h
 EXPORTS = ("shk_build", "shk_build_stats", "shk_query", "shk_serialize", "shk_deserialize",
            "shk_size_bits", "shk_free", "shk_last_error", "shk_leaf_search", "shk_leaf_search_noalloc",
-           "shk_version")
+           "shk_leaf_tune", "shk_leaf_configs", "shk_leaf_graph_replays", "shk_version")
 
 
 class ShkError(RuntimeError):
@@ -43,7 +43,7 @@ class _Keys(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in
                 ("leaf_size", "bucket_size", "shard_buckets", "eps_num", "sched", "seeds_per_lane",
-                 "chunk_passes", "profile")]
+                 "chunk_passes", "profile", "warps_per_block", "key_unroll")]
 
 
 _STAT_U64 = ["n_keys", "n_buckets", "n_leaves", "n_search_leaves", "n_split_nodes", "leaf_seeds_min",
@@ -54,7 +54,7 @@ _STAT_F64 = ["ms_fingerprint", "ms_partition", "ms_split", "ms_leaf", "ms_orient
 
 class _Stats(ctypes.Structure):
     _fields_ = ([(n, ctypes.c_uint64) for n in _STAT_U64] + [(n, ctypes.c_double) for n in _STAT_F64]
-                + [("leaf_launches", ctypes.c_uint64)])
+                + [("leaf_launches", ctypes.c_uint64), ("leaf_cfg", ctypes.c_uint32 * 4)])
 
 
 _lib = None
@@ -80,6 +80,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "shk_last_error": (ctypes.c_char_p, []),
         "shk_leaf_search": (i32, [vp, vp, u32, u64, vp, vp, vp]),
         "shk_leaf_search_noalloc": (i32, [vp, vp, u32, u64, vp, vp, vp]),
+        "shk_leaf_tune": (i32, [u32, vp, vp, i32, vp]),
+        "shk_leaf_configs": (u32, [vp, u32]),
+        "shk_leaf_graph_replays": (u64, []),
         "shk_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -184,11 +187,11 @@ class Mphf:
 def shk_build(keys, leaf_size: int, bucket_size: int, *, kind: int = SHK_KEYS_U64, str_offsets=None,
               shard_buckets: int = 0, eps_num: int = 0, sched: int = SHK_SCHED_PERSISTENT,
               seeds_per_lane: int = 0, chunk_passes: int = 0, profile: bool = False,
-              stream=None) -> Mphf:
+              warps_per_block: int = 0, key_unroll: int = 0, stream=None) -> Mphf:
     lib = load_library()
     k, keep = _as_keys(keys, kind, str_offsets)
     o = _Opts(leaf_size, bucket_size, shard_buckets, eps_num, sched, seeds_per_lane, chunk_passes,
-              1 if profile else 0)
+              1 if profile else 0, warps_per_block, key_unroll)
     out = ctypes.c_void_p()
     _check(lib.shk_build(ctypes.byref(k), ctypes.byref(o), _stream_handle(stream), ctypes.byref(out)))
     del keep
@@ -198,7 +201,9 @@ def shk_build(keys, leaf_size: int, bucket_size: int, *, kind: int = SHK_KEYS_U6
 def shk_build_stats(handle) -> dict:
     s = _Stats()
     _check(load_library().shk_build_stats(handle, ctypes.byref(s)))
-    return {name: getattr(s, name) for name, _ in _Stats._fields_}
+    out = {name: getattr(s, name) for name, _ in _Stats._fields_}
+    out["leaf_cfg"] = list(s.leaf_cfg)
+    return out
 
 
 def shk_query(handle, keys, *, kind: int = SHK_KEYS_U64, str_offsets=None, out=None, stream=None):
@@ -251,19 +256,25 @@ def shk_version() -> str:
     return load_library().shk_version().decode()
 
 
-def shk_leaf_search(leaf_keys, leaf_off, seed_start: int = 0, want_f: bool = True, stream=None):
+def shk_leaf_search(leaf_keys, leaf_off, seed_start: int = 0, want_f: bool = True, stream=None,
+                    seeds_out=None, f_out=None):
     """Batched leaf search on device tensors: leaf_keys (int64/uint64 bits,
     the 64-bit leaf inputs), leaf_off (int32, n_leaves + 1 offsets).  Returns
-    (seeds, f_masks) as device int64 tensors (f_masks None if not wanted)."""
+    (seeds, f_masks) as device int64 tensors (f_masks None if not wanted).
+    Passing the same tensors again (seeds_out / f_out included) replays the
+    library's captured CUDA graph."""
     torch = _torch()
     lib = load_library()
     if not (leaf_keys.is_cuda and leaf_off.is_cuda):
         raise ValueError("shk_leaf_search takes device tensors")
-    kk = leaf_keys.contiguous()
-    off = leaf_off.contiguous()
+    kk = leaf_keys if leaf_keys.is_contiguous() else leaf_keys.contiguous()
+    off = leaf_off if leaf_off.is_contiguous() else leaf_off.contiguous()
     nl = off.numel() - 1
-    seeds = torch.empty(max(nl, 1), dtype=torch.int64, device=kk.device)
-    f = torch.empty(max(nl, 1), dtype=torch.int64, device=kk.device) if want_f else None
+    seeds = seeds_out if seeds_out is not None else torch.empty(max(nl, 1), dtype=torch.int64, device=kk.device)
+    if f_out is not None:
+        f = f_out
+    else:
+        f = torch.empty(max(nl, 1), dtype=torch.int64, device=kk.device) if want_f else None
     _check(lib.shk_leaf_search(kk.data_ptr(), off.data_ptr(), nl, seed_start, seeds.data_ptr(),
                                f.data_ptr() if f is not None else None, _stream_handle(stream)))
     return seeds[:nl], (f[:nl] if f is not None else None)
@@ -284,3 +295,32 @@ def shk_leaf_search_noalloc(leaf_keys, leaf_off, seeds_out, f_out=None, seed_sta
                                        seeds_out.data_ptr(), f_out.data_ptr() if f_out is not None else None,
                                        _stream_handle(stream)))
     return seeds_out, f_out
+
+
+def shk_leaf_configs() -> list[tuple[int, int, int]]:
+    """Supported leaf kernel configurations (seeds per lane, warps per block, unroll)."""
+    lib = load_library()
+    buf = (ctypes.c_uint32 * 256)()
+    n = lib.shk_leaf_configs(buf, 64)
+    return [(buf[4 * i], buf[4 * i + 1], buf[4 * i + 2]) for i in range(n)]
+
+
+def shk_leaf_tune(leaf_size: int, probe_all: bool = False) -> dict:
+    """The autotuner's leaf kernel configuration for leaf_size on the current
+    device, its measured key-seed evaluations/s, and (probe_all) every
+    configuration's rate."""
+    lib = load_library()
+    cfg = (ctypes.c_uint32 * 4)()
+    rate = ctypes.c_double()
+    n = len(shk_leaf_configs())
+    allr = (ctypes.c_double * max(n, 1))()
+    _check(lib.shk_leaf_tune(leaf_size, cfg, ctypes.byref(rate), int(probe_all), allr))
+    out = {"seeds_per_lane": cfg[0], "warps_per_block": cfg[1], "key_unroll": cfg[2], "passes": cfg[3],
+           "evals_per_s": rate.value}
+    if probe_all:
+        out["all"] = [{"cfg": c, "evals_per_s": allr[i]} for i, c in enumerate(shk_leaf_configs())]
+    return out
+
+
+def shk_leaf_graph_replays() -> int:
+    return int(load_library().shk_leaf_graph_replays())

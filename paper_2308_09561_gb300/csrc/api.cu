@@ -61,8 +61,6 @@ struct PhaseTimer {
   }
 };
 
-static uint32_t default_seeds_per_lane(uint32_t n) { return n <= 8 ? 1u : 4u; }
-static uint32_t default_passes(uint32_t n) { return n <= 24 ? 4u : 8u; }
 
 __global__ void k_u64_to_u32(const uint64_t* in, uint64_t n, uint32_t* out) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -164,12 +162,19 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   if (o->sched > SHK_SCHED_PER_BUCKET) return fail(SHK_EINVAL, "unknown schedule");
   const uint32_t S = o->shard_buckets ? o->shard_buckets : std::max(1u, 8192u / b);
   const uint32_t eps = o->eps_num ? o->eps_num : kDefaultEpsNum;
-  const uint32_t U = o->seeds_per_lane ? o->seeds_per_lane : default_seeds_per_lane(n);
-  const uint32_t passes = o->chunk_passes ? o->chunk_passes : default_passes(n);
-  if (U != 1 && U != 2 && U != 4) return fail(SHK_EINVAL, "seeds_per_lane must be 1, 2 or 4");
-
   Ctx c(st);
   SHK_TRY(init_ctx(c));
+  // leaf kernel configuration: the autotuner's choice for this leaf size,
+  // unless the caller fixes it
+  LeafCfg cfg;
+  if (o->seeds_per_lane) {
+    cfg = {o->seeds_per_lane, o->warps_per_block ? o->warps_per_block : 8u,
+           o->key_unroll ? o->key_unroll : 2u, o->chunk_passes ? o->chunk_passes : 8u};
+    if (!leaf_cfg_valid(cfg)) return fail(SHK_EINVAL, "unsupported leaf kernel configuration");
+  } else {
+    SHK_TRY(tuned_leaf_cfg(c, n, &cfg));
+    if (o->chunk_passes) cfg.passes = o->chunk_passes;
+  }
   PhaseTimer pt(o->profile != 0, st);
   const int t0 = pt.mark();
   const uint64_t B = N ? (N + b - 1) / b : 0;
@@ -243,15 +248,15 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   SHK_TRY(c.arena.alloc(&best, h_L));
   SHK_TRY(c.arena.alloc(&counters, 4, true));  // executed, sum(seed+1), sum((seed+1) m)
   if (h_L) SHK_CUDA(cudaMemsetAsync(best, 0xFF, (size_t)h_L * 8, st));
-  LeafSearchArgs a{leaves, h_L, llo, 0, best, err, counters, U, passes};
+  LeafSearchArgs a{leaves, h_L, llo, 0, best, err, counters, cfg};
   uint64_t leaf_launches = 0;
   if (o->sched == SHK_SCHED_PERSISTENT) {
-    SHK_TRY(launch_leaf_persistent(c, a, n));
+    SHK_TRY(launch_leaf_persistent(c, a));
     leaf_launches = h_L ? 1 : 0;
   } else {
     for (uint64_t i = 0; i < B; i++) {
       if (h_leaf_base[i + 1] > h_leaf_base[i]) {
-        SHK_TRY(launch_leaf_range(c, a, h_leaf_base[i], h_leaf_base[i + 1], n));
+        SHK_TRY(launch_leaf_range(c, a, h_leaf_base[i], h_leaf_base[i + 1]));
         leaf_launches++;
       }
     }
@@ -362,6 +367,10 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   s.ms_encode = pt.ms(t5, t6);
   s.ms_ribbon = pt.ms(t6, t7);
   s.ms_total = pt.ms(t0, t7);
+  s.leaf_cfg[0] = cfg.seeds_per_lane;
+  s.leaf_cfg[1] = cfg.warps;
+  s.leaf_cfg[2] = cfg.unroll;
+  s.leaf_cfg[3] = cfg.passes;
   *out = m;
   return SHK_OK;
 }
@@ -495,6 +504,42 @@ extern "C" shk_status shk_query(const shk_mphf* m, const shk_keys* keys, uint64_
   return s;
 }
 
+// The batched leaf search runs as one captured CUDA graph (descriptor kernel,
+// state clears, the persistent search, orientation).  The instantiated graph
+// and its working buffers are cached per host thread and replayed while the
+// call's pointers, sizes and kernel configuration stay the same; a replay
+// reads the buffers' current contents.
+struct LeafGraph {
+  bool valid = false;
+  const uint64_t* keys = nullptr;
+  const uint32_t* off = nullptr;
+  uint32_t n = 0;
+  uint64_t seed_start = 0;
+  uint64_t* seeds = nullptr;
+  uint64_t* fmask = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = -1;
+  LeafCfg cfg{};
+  cudaGraphExec_t exec = nullptr;
+  LeafDesc* d = nullptr;
+  uint32_t* state = nullptr;             // work-distribution state
+  unsigned long long* flags = nullptr;   // [0] seed counter, [1] error word
+  uint64_t replays = 0;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (d) cudaFree(d);
+    if (state) cudaFree(state);
+    if (flags) cudaFree(flags);
+    exec = nullptr;
+    d = nullptr;
+    state = nullptr;
+    flags = nullptr;
+    valid = false;
+  }
+};
+static thread_local LeafGraph g_leaf_graph;
+static thread_local cudaStream_t g_capture_stream[64];
+
 extern "C" shk_status shk_leaf_search(const uint64_t* leaf_keys, const uint32_t* leaf_off,
                                       uint32_t n_leaves, uint64_t seed_start, uint64_t* seeds_out,
                                       uint64_t* f_out, void* cuda_stream) {
@@ -503,27 +548,115 @@ extern "C" shk_status shk_leaf_search(const uint64_t* leaf_keys, const uint32_t*
   Ctx c(st);
   SHK_TRY(init_ctx(c));
   if (n_leaves == 0) return SHK_OK;
+  if (c.device < 0 || c.device >= 64) return fail(SHK_EINVAL, "device ordinal out of range");
+  // the legacy default stream cannot be captured: use a blocking stream of
+  // the library, which is ordered with it
+  cudaStream_t run_st = st;
+  if (st == nullptr) {
+    if (!g_capture_stream[c.device]) SHK_CUDA(cudaStreamCreate(&g_capture_stream[c.device]));
+    run_st = g_capture_stream[c.device];
+  }
+  LeafCfg cfg;
+  SHK_TRY(tuned_leaf_cfg(c, kMaxLeaf, &cfg));
+  LeafGraph& g = g_leaf_graph;
+  const bool hit = g.valid && g.keys == leaf_keys && g.off == leaf_off && g.n == n_leaves &&
+                   g.seed_start == seed_start && g.seeds == seeds_out && g.fmask == f_out &&
+                   g.stream == run_st && g.device == c.device &&
+                   memcmp(&g.cfg, &cfg, sizeof cfg) == 0;
+  const uint32_t L = n_leaves;
+  const size_t state_words = (size_t)L + (L + 31) / 32 + 1;
+  if (!hit) {
+    g.release();
+    SHK_CUDA(cudaMalloc(&g.d, (size_t)L * sizeof(LeafDesc)));
+    SHK_CUDA(cudaMalloc(&g.state, state_words * sizeof(uint32_t)));
+    // 64-bit atomics need 8-byte alignment: the flags get their own allocation
+    SHK_CUDA(cudaMalloc(&g.flags, 2 * sizeof(unsigned long long)));
+    unsigned long long* counter = g.flags;
+    uint32_t* err = (uint32_t*)(g.flags + 1);
+    Ctx cc(run_st);
+    cc.num_sms = c.num_sms;
+    cc.device = c.device;
+    SHK_CUDA(cudaStreamBeginCapture(run_st, cudaStreamCaptureModeThreadLocal));
+    auto capture = [&]() -> shk_status {
+      SHK_CUDA(cudaMemsetAsync(g.flags, 0, 2 * sizeof(unsigned long long), run_st));
+      k_leaf_descs<<<(L + 255) / 256, 256, 0, run_st>>>(leaf_off, L, g.d);
+      SHK_CUDA(cudaGetLastError());
+      SHK_CUDA(cudaMemsetAsync(seeds_out, 0xFF, (size_t)L * 8, run_st));
+      LeafSearchArgs a{g.d, L, leaf_keys, seed_start, (unsigned long long*)seeds_out, err, counter, cfg};
+      SHK_TRY(launch_leaf_persistent_state(cc, a, g.state));
+      SHK_TRY(launch_orient(cc, g.d, L, leaf_keys, (unsigned long long*)seeds_out, nullptr, nullptr,
+                            f_out, err));
+      return SHK_OK;
+    };
+    const shk_status cs = capture();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(run_st, &graph);
+    if (cs != SHK_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      g.release();
+      return cs;
+    }
+    if (ee != cudaSuccess) {
+      g.release();
+      return fail(SHK_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ee));
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      g.release();
+      return fail(SHK_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    }
+    g.keys = leaf_keys;
+    g.off = leaf_off;
+    g.n = L;
+    g.seed_start = seed_start;
+    g.seeds = seeds_out;
+    g.fmask = f_out;
+    g.stream = run_st;
+    g.device = c.device;
+    g.cfg = cfg;
+    g.valid = true;
+  }
+  uint32_t h_err = 0;
   auto run = [&]() -> shk_status {
-    LeafDesc* d;
-    uint32_t* err;
-    unsigned long long* counters;
-    SHK_TRY(c.arena.alloc(&d, n_leaves));
-    SHK_TRY(c.arena.alloc(&err, 1, true));
-    SHK_TRY(c.arena.alloc(&counters, 1, true));
-    k_leaf_descs<<<(n_leaves + 255) / 256, 256, 0, st>>>(leaf_off, n_leaves, d);
-    c.launches++;
-    SHK_CUDA(cudaMemsetAsync(seeds_out, 0xFF, (size_t)n_leaves * 8, st));
-    LeafSearchArgs a{d, n_leaves, leaf_keys, seed_start, (unsigned long long*)seeds_out, err,
-                     counters, 4, 8};
-    SHK_TRY(launch_leaf_persistent(c, a, kMaxLeaf));
-    SHK_TRY(launch_orient(c, d, n_leaves, leaf_keys, (unsigned long long*)seeds_out, nullptr,
-                          nullptr, f_out, err));
-    uint32_t h_err = 0;
-    SHK_CUDA(cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, st));
-    SHK_CUDA(cudaStreamSynchronize(st));
+    SHK_CUDA(cudaGraphLaunch(g.exec, run_st));
+    g.replays++;
+    SHK_CUDA(cudaMemcpyAsync(&h_err, (const uint32_t*)(g.flags + 1), 4, cudaMemcpyDeviceToHost, run_st));
+    SHK_CUDA(cudaStreamSynchronize(run_st));
     return device_errors(h_err);
   };
-  shk_status s = run();
-  if (s != SHK_OK) cudaStreamSynchronize(st);
+  const shk_status s = run();
+  if (s != SHK_OK) cudaStreamSynchronize(run_st);
   return s;
+}
+
+extern "C" uint64_t shk_leaf_graph_replays(void) { return g_leaf_graph.replays; }
+
+extern "C" shk_status shk_leaf_tune(uint32_t leaf_size, uint32_t* cfg_out, double* evals_per_s,
+                                    int probe_all, double* all_evals_per_s) {
+  if (leaf_size < 2 || leaf_size > kMaxLeaf || !cfg_out) return fail(SHK_EINVAL, "bad argument");
+  Ctx c(nullptr);
+  SHK_TRY(init_ctx(c));
+  LeafCfg cfg;
+  SHK_TRY(tuned_leaf_cfg(c, leaf_size, &cfg));
+  cfg_out[0] = cfg.seeds_per_lane;
+  cfg_out[1] = cfg.warps;
+  cfg_out[2] = cfg.unroll;
+  cfg_out[3] = cfg.passes;
+  if (evals_per_s) SHK_TRY(probe_leaf_cfg(c, cfg, leaf_size, evals_per_s));
+  if (probe_all && all_evals_per_s)
+    for (int i = 0; i < leaf_cfg_count(); i++) SHK_TRY(probe_leaf_cfg(c, leaf_cfg_at(i), leaf_size, &all_evals_per_s[i]));
+  return SHK_OK;
+}
+
+extern "C" uint32_t shk_leaf_configs(uint32_t* cfgs, uint32_t cap) {
+  const uint32_t n = (uint32_t)leaf_cfg_count();
+  for (uint32_t i = 0; i < n && i < cap; i++) {
+    const LeafCfg c = leaf_cfg_at((int)i);
+    cfgs[4 * i] = c.seeds_per_lane;
+    cfgs[4 * i + 1] = c.warps;
+    cfgs[4 * i + 2] = c.unroll;
+    cfgs[4 * i + 3] = c.passes;
+  }
+  return n;
 }

@@ -45,6 +45,11 @@ shk_status launch_split(Ctx& c, const uint64_t* slo, const uint64_t* shi, const 
                         LeafDesc* leaves, uint64_t* llo, uint64_t* lhi, uint32_t* err);
 
 // a4 + a5: leaf seed search.  best[L] must be preset to ~0.
+// Kernel configuration: seeds per lane, warps per block, key-loop unroll and
+// passes (of 32 x seeds_per_lane seeds) per work item.  It changes speed only.
+struct LeafCfg {
+  uint32_t seeds_per_lane, warps, unroll, passes;
+};
 struct LeafSearchArgs {
   const LeafDesc* leaves;
   uint32_t n_leaves;
@@ -53,15 +58,19 @@ struct LeafSearchArgs {
   unsigned long long* best;
   uint32_t* err;
   unsigned long long* executed;  // seeds evaluated (counter)
-  uint32_t seeds_per_lane;       // 1, 2 or 4
-  uint32_t passes;               // passes per work item
+  LeafCfg cfg;
 };
-shk_status launch_leaf_persistent(Ctx& c, const LeafSearchArgs& a, uint32_t max_m);
+shk_status launch_leaf_persistent(Ctx& c, const LeafSearchArgs& a);
 // As launch_leaf_persistent, with caller-owned state of
 // (n_leaves + (n_leaves + 31) / 32 + 1) u32 words (cleared by the launch).
 shk_status launch_leaf_persistent_state(Ctx& c, const LeafSearchArgs& a, uint32_t* state);
-shk_status launch_leaf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1,
-                             uint32_t max_m);
+shk_status launch_leaf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1);
+// autotuner: the fastest configuration for leaves of m keys on this device
+shk_status tuned_leaf_cfg(Ctx& c, uint32_t m, LeafCfg* out);
+shk_status probe_leaf_cfg(Ctx& c, const LeafCfg& cfg, uint32_t m, double* evals_per_s);
+bool leaf_cfg_valid(const LeafCfg& c);
+int leaf_cfg_count();
+LeafCfg leaf_cfg_at(int i);
 // a6: orientation; writes seeds into codes[code_idx], f per key (leaf order)
 // and optionally f as a mask per leaf.
 shk_status launch_orient(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves, const uint64_t* x,

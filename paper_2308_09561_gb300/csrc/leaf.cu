@@ -11,12 +11,13 @@
 // lanes hash the edges into shared memory and lane 0 runs a union-find with
 // tree/pseudotree labels.  Seeds are taken in increasing order, so the first
 // survivor that passes is the leaf's minimum seed within the work item.
+#include <algorithm>
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace shk {
 
-constexpr int kLeafThreads = 256;
-constexpr int kLeafWarps = kLeafThreads / 32;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct WarpScratch {
@@ -93,7 +94,7 @@ __device__ __forceinline__ uint64_t read_uniform(const volatile unsigned long lo
 // below the seeds still to test).  Called by a whole warp; *done counts the
 // seeds evaluated.
 
-template <int U, bool WIDE>
+template <int U, int UNROLL, bool WIDE>
 __device__ uint64_t search_seeds(WarpScratch* ws, uint32_t m, uint64_t s0, uint32_t passes,
                                  const volatile unsigned long long* best, uint32_t* done) {
   const uint32_t lane = threadIdx.x & 31;
@@ -112,7 +113,7 @@ __device__ uint64_t search_seeds(WarpScratch* ws, uint32_t m, uint64_t s0, uint3
       mlo[u] = 0;
       mhi[u] = 0;
     }
-#pragma unroll 2
+#pragma unroll UNROLL
     for (uint32_t i = 0; i < m; i++) {
       const uint64_t x = ws->x[i];
 #pragma unroll
@@ -148,13 +149,13 @@ __device__ uint64_t search_seeds(WarpScratch* ws, uint32_t m, uint64_t s0, uint3
   return ~0ull;
 }
 
-template <int U>
+template <int U, int UNROLL>
 __device__ __forceinline__ uint64_t search_dispatch(WarpScratch* ws, uint32_t m, uint64_t s0,
                                                     uint32_t passes,
                                                     const volatile unsigned long long* best,
                                                     uint32_t* done) {
-  return m > 32 ? search_seeds<U, true>(ws, m, s0, passes, best, done)
-                : search_seeds<U, false>(ws, m, s0, passes, best, done);
+  return m > 32 ? search_seeds<U, UNROLL, true>(ws, m, s0, passes, best, done)
+                : search_seeds<U, UNROLL, false>(ws, m, s0, passes, best, done);
 }
 
 __device__ __forceinline__ void load_leaf(WarpScratch* ws, const LeafDesc& d, const uint64_t* x) {
@@ -198,16 +199,16 @@ __device__ uint32_t find_open_leaf(const uint32_t* closed, uint32_t n_leaves, ui
 // counter; a found seed is committed with atomicMin, so the result is the
 // minimum whatever the schedule: every chunk below the final minimum was
 // handed out before the chunk that found it and is searched to its end.
-template <int U>
-__global__ void __launch_bounds__(kLeafThreads)
+template <int U, int WARPS, int UNROLL>
+__global__ void __launch_bounds__(WARPS * 32)
     k_leaf_persistent(const LeafDesc* __restrict__ leaves, uint32_t n_leaves,
                       const uint64_t* __restrict__ x, uint64_t seed_start, uint32_t passes,
                       unsigned long long* best, uint32_t* next_chunk, uint32_t* closed,
                       uint32_t* next_leaf, unsigned long long* executed, uint32_t* err) {
-  __shared__ WarpScratch scratch[kLeafWarps];
+  __shared__ WarpScratch scratch[WARPS];
   const uint32_t lane = threadIdx.x & 31;
   WarpScratch* ws = &scratch[threadIdx.x >> 5];
-  const uint32_t gw = blockIdx.x * kLeafWarps + (threadIdx.x >> 5);
+  const uint32_t gw = blockIdx.x * WARPS + (threadIdx.x >> 5);
   const uint32_t nwords = (n_leaves + 31) / 32;
   uint32_t pos = nwords ? (uint32_t)(((uint64_t)gw * 2654435761u) % nwords) : 0;
   const uint64_t chunk = (uint64_t)passes * 32u * U;
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(kLeafThreads)
         break;
       }
       uint32_t done = 0;
-      const uint64_t r = search_dispatch<U>(ws, d.m, s0, passes, &best[leaf], &done);
+      const uint64_t r = search_dispatch<U, UNROLL>(ws, d.m, s0, passes, &best[leaf], &done);
       done_seeds += done;
       if (r != ~0ull) {
         if (lane == 0) {
@@ -263,15 +264,15 @@ __global__ void __launch_bounds__(kLeafThreads)
 
 // One warp per leaf, no sharing: the plain form that is launched once per
 // bucket over that bucket's leaves.
-template <int U>
-__global__ void __launch_bounds__(kLeafThreads)
+template <int U, int WARPS, int UNROLL>
+__global__ void __launch_bounds__(WARPS * 32)
     k_leaf_range(const LeafDesc* __restrict__ leaves, uint32_t l0, uint32_t l1,
                  const uint64_t* __restrict__ x, uint64_t seed_start, uint32_t passes,
                  unsigned long long* best, unsigned long long* executed, uint32_t* err) {
-  __shared__ WarpScratch scratch[kLeafWarps];
+  __shared__ WarpScratch scratch[WARPS];
   const uint32_t lane = threadIdx.x & 31;
   WarpScratch* ws = &scratch[threadIdx.x >> 5];
-  const uint32_t leaf = l0 + blockIdx.x * kLeafWarps + (threadIdx.x >> 5);
+  const uint32_t leaf = l0 + blockIdx.x * WARPS + (threadIdx.x >> 5);
   if (leaf >= l1) return;
   const LeafDesc d = leaves[leaf];
   load_leaf(ws, d, x);
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(kLeafThreads)
       break;
     }
     uint32_t done = 0;
-    const uint64_t r = search_dispatch<U>(ws, d.m, s0, passes, nullptr, &done);
+    const uint64_t r = search_dispatch<U, UNROLL>(ws, d.m, s0, passes, nullptr, &done);
     done_seeds += done;
     if (r != ~0ull) {
       if (lane == 0) best[leaf] = r;
@@ -293,93 +294,203 @@ __global__ void __launch_bounds__(kLeafThreads)
   if (lane == 0) atomicAdd(executed, done_seeds);
 }
 
-template <int U>
-static shk_status launch_persistent_u(Ctx& c, const LeafSearchArgs& a) {
-  uint32_t* state;
+// Throughput probe for the tuner: every warp searches fixed seed ranges of a
+// synthetic leaf of m keys and counts the seeds it evaluated.
+template <int U, int WARPS, int UNROLL>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_leaf_probe(const uint64_t* __restrict__ keys, uint32_t m, uint32_t rounds,
+                 unsigned long long* executed) {
+  __shared__ WarpScratch scratch[WARPS];
+  const uint32_t lane = threadIdx.x & 31;
+  WarpScratch* ws = &scratch[threadIdx.x >> 5];
+  const uint32_t gw = blockIdx.x * WARPS + (threadIdx.x >> 5);
+  for (uint32_t i = lane; i < m; i += 32) ws->x[i] = keys[(uint64_t)gw * kMaxLeaf + i];
+  __syncwarp();
+  uint32_t done = 0;
+  for (uint32_t r = 0; r < rounds; r++)
+    (void)search_dispatch<U, UNROLL>(ws, m, (uint64_t)r << 32, 4, nullptr, &done);
+  if (lane == 0) atomicAdd(executed, (unsigned long long)done);
+}
+
+__global__ void k_probe_keys(uint64_t* keys, uint64_t n, uint64_t salt) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) keys[i] = mix64(salt + i * 0x9E3779B97F4A7C15ull);
+}
+
+// ---------------------------------------------------------------------------
+// configurations: seeds per lane x warps per block x key-loop unroll
+// ---------------------------------------------------------------------------
+struct LeafKernels {
+  LeafCfg cfg;
+  void (*persistent)(const LeafDesc*, uint32_t, const uint64_t*, uint64_t, uint32_t,
+                     unsigned long long*, uint32_t*, uint32_t*, uint32_t*, unsigned long long*,
+                     uint32_t*);
+  void (*range)(const LeafDesc*, uint32_t, uint32_t, const uint64_t*, uint64_t, uint32_t,
+                unsigned long long*, unsigned long long*, uint32_t*);
+  void (*probe)(const uint64_t*, uint32_t, uint32_t, unsigned long long*);
+};
+
+#define SHK_LEAF_CFG(U, W, R) \
+  {{U, W, R, 0}, k_leaf_persistent<U, W, R>, k_leaf_range<U, W, R>, k_leaf_probe<U, W, R>}
+
+static const LeafKernels kLeafTable[] = {
+    SHK_LEAF_CFG(1, 8, 2), SHK_LEAF_CFG(2, 4, 2), SHK_LEAF_CFG(2, 8, 2), SHK_LEAF_CFG(2, 8, 4),
+    SHK_LEAF_CFG(2, 16, 2), SHK_LEAF_CFG(4, 4, 2), SHK_LEAF_CFG(4, 8, 1), SHK_LEAF_CFG(4, 8, 2),
+    SHK_LEAF_CFG(4, 8, 4), SHK_LEAF_CFG(4, 16, 2)};
+constexpr int kNumLeafCfg = sizeof(kLeafTable) / sizeof(kLeafTable[0]);
+
+static const LeafKernels* find_kernels(const LeafCfg& c) {
+  for (int i = 0; i < kNumLeafCfg; i++) {
+    const LeafCfg& t = kLeafTable[i].cfg;
+    if (t.seeds_per_lane == c.seeds_per_lane && t.warps == c.warps && t.unroll == c.unroll)
+      return &kLeafTable[i];
+  }
+  return nullptr;
+}
+
+bool leaf_cfg_valid(const LeafCfg& c) { return find_kernels(c) != nullptr && c.passes >= 1; }
+
+int leaf_cfg_count() { return kNumLeafCfg; }
+
+LeafCfg leaf_cfg_at(int i) { return kLeafTable[i].cfg; }
+
+static shk_status persistent_blocks(Ctx& c, const LeafKernels* k, uint32_t* blocks) {
+  int per_sm = 0;
+  SHK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->persistent,
+                                                         (int)k->cfg.warps * 32, 0));
+  if (per_sm < 1) per_sm = 1;
+  *blocks = (uint32_t)(c.num_sms * per_sm);
+  return SHK_OK;
+}
+
+// 64-bit atomics (seed minimum, seed counter) need 8-byte aligned targets.
+static bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+
+static shk_status launch_persistent_with(Ctx& c, const LeafSearchArgs& a, uint32_t* state) {
+  const LeafKernels* k = find_kernels(a.cfg);
+  if (!k) return fail(SHK_EINVAL, "unsupported leaf kernel configuration");
+  if (!aligned8(a.best) || !aligned8(a.executed) || !aligned8(a.x))
+    return fail(SHK_EINVAL, "seed, counter and key buffers must be 8-byte aligned");
   const uint32_t L = a.n_leaves;
   const uint32_t nwords = (L + 31) / 32;
-  // next_chunk[L] | closed[nwords] | next_leaf[1]
-  SHK_TRY(c.arena.alloc(&state, (size_t)L + nwords + 1, true));
-  int per_sm = 0;
-  SHK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_persistent<U>,
-                                                         kLeafThreads, 0));
-  if (per_sm < 1) per_sm = 1;
-  const uint32_t blocks = (uint32_t)(c.num_sms * per_sm);
-  k_leaf_persistent<U><<<blocks, kLeafThreads, 0, c.stream>>>(
-      a.leaves, L, a.x, a.seed_start, a.passes, a.best, state, state + L, state + L + nwords,
+  uint32_t blocks;
+  SHK_TRY(persistent_blocks(c, k, &blocks));
+  k->persistent<<<blocks, k->cfg.warps * 32, 0, c.stream>>>(
+      a.leaves, L, a.x, a.seed_start, a.cfg.passes, a.best, state, state + L, state + L + nwords,
       a.executed, a.err);
   c.launches++;
   SHK_CUDA(cudaGetLastError());
   return SHK_OK;
 }
 
-shk_status launch_leaf_persistent(Ctx& c, const LeafSearchArgs& a, uint32_t max_m) {
-  (void)max_m;
+shk_status launch_leaf_persistent(Ctx& c, const LeafSearchArgs& a) {
   if (a.n_leaves == 0) return SHK_OK;
-  switch (a.seeds_per_lane) {
-    case 1:
-      return launch_persistent_u<1>(c, a);
-    case 2:
-      return launch_persistent_u<2>(c, a);
-    default:
-      return launch_persistent_u<4>(c, a);
-  }
+  uint32_t* state;
+  const uint32_t L = a.n_leaves;
+  // next_chunk[L] | closed[(L + 31) / 32] | next_leaf[1]
+  SHK_TRY(c.arena.alloc(&state, (size_t)L + (L + 31) / 32 + 1, true));
+  return launch_persistent_with(c, a, state);
 }
 
 // Same launch with the work-distribution state supplied by the caller:
 // state = next_chunk[L] | closed[(L + 31) / 32] | next_leaf[1], zeroed here.
-template <int U>
-static shk_status launch_persistent_state_u(Ctx& c, const LeafSearchArgs& a, uint32_t* state) {
-  const uint32_t L = a.n_leaves;
-  const uint32_t nwords = (L + 31) / 32;
-  SHK_CUDA(cudaMemsetAsync(state, 0, ((size_t)L + nwords + 1) * sizeof(uint32_t), c.stream));
-  int per_sm = 0;
-  SHK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_persistent<U>,
-                                                         kLeafThreads, 0));
-  if (per_sm < 1) per_sm = 1;
-  const uint32_t blocks = (uint32_t)(c.num_sms * per_sm);
-  k_leaf_persistent<U><<<blocks, kLeafThreads, 0, c.stream>>>(
-      a.leaves, L, a.x, a.seed_start, a.passes, a.best, state, state + L, state + L + nwords,
-      a.executed, a.err);
-  c.launches++;
-  SHK_CUDA(cudaGetLastError());
-  return SHK_OK;
-}
-
 shk_status launch_leaf_persistent_state(Ctx& c, const LeafSearchArgs& a, uint32_t* state) {
   if (a.n_leaves == 0) return SHK_OK;
-  switch (a.seeds_per_lane) {
-    case 1:
-      return launch_persistent_state_u<1>(c, a, state);
-    case 2:
-      return launch_persistent_state_u<2>(c, a, state);
-    default:
-      return launch_persistent_state_u<4>(c, a, state);
-  }
+  const uint32_t L = a.n_leaves;
+  SHK_CUDA(cudaMemsetAsync(state, 0, ((size_t)L + (L + 31) / 32 + 1) * sizeof(uint32_t), c.stream));
+  return launch_persistent_with(c, a, state);
 }
 
-template <int U>
-static shk_status launch_range_u(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1) {
-  const uint32_t blocks = (l1 - l0 + kLeafWarps - 1) / kLeafWarps;
-  k_leaf_range<U><<<blocks, kLeafThreads, 0, c.stream>>>(a.leaves, l0, l1, a.x, a.seed_start,
-                                                         a.passes, a.best, a.executed, a.err);
+shk_status launch_leaf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1) {
+  if (l1 <= l0) return SHK_OK;
+  const LeafKernels* k = find_kernels(a.cfg);
+  if (!k) return fail(SHK_EINVAL, "unsupported leaf kernel configuration");
+  if (!aligned8(a.best) || !aligned8(a.executed) || !aligned8(a.x))
+    return fail(SHK_EINVAL, "seed, counter and key buffers must be 8-byte aligned");
+  const uint32_t W = k->cfg.warps;
+  const uint32_t blocks = (l1 - l0 + W - 1) / W;
+  k->range<<<blocks, W * 32, 0, c.stream>>>(a.leaves, l0, l1, a.x, a.seed_start, a.cfg.passes,
+                                            a.best, a.executed, a.err);
   c.launches++;
   SHK_CUDA(cudaGetLastError());
   return SHK_OK;
 }
 
-shk_status launch_leaf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1,
-                             uint32_t max_m) {
-  (void)max_m;
-  if (l1 <= l0) return SHK_OK;
-  switch (a.seeds_per_lane) {
-    case 1:
-      return launch_range_u<1>(c, a, l0, l1);
-    case 2:
-      return launch_range_u<2>(c, a, l0, l1);
-    default:
-      return launch_range_u<4>(c, a, l0, l1);
+// ---------------------------------------------------------------------------
+// Autotuner: for each leaf-size bin (m <= 16, 17-32, 33-48, 49-64) time every
+// configuration on synthetic leaves of the bin's largest size and keep the
+// fastest (key-seed evaluations per second).  Results are cached per device.
+// The configuration never changes results, only speed.
+// ---------------------------------------------------------------------------
+struct TuneSlot {
+  bool done = false;
+  LeafCfg cfg{4, 8, 2, 8};
+  double evals_per_s = 0;
+};
+static std::mutex g_tune_mutex;
+static TuneSlot g_tune[64][4];
+
+static uint32_t default_passes(uint32_t m) { return m <= 16 ? 2u : (m <= 32 ? 4u : 8u); }
+
+shk_status probe_leaf_cfg(Ctx& c, const LeafCfg& cfg, uint32_t m, double* evals_per_s) {
+  const LeafKernels* k = find_kernels(cfg);
+  if (!k) return fail(SHK_EINVAL, "unsupported leaf kernel configuration");
+  uint32_t blocks;
+  SHK_TRY(persistent_blocks(c, k, &blocks));
+  const uint64_t warps = (uint64_t)blocks * cfg.warps;
+  uint64_t* keys;
+  unsigned long long* cnt;
+  SHK_TRY(c.arena.alloc(&keys, warps * kMaxLeaf));
+  SHK_TRY(c.arena.alloc(&cnt, 1, true));
+  k_probe_keys<<<(unsigned)((warps * kMaxLeaf + 255) / 256), 256, 0, c.stream>>>(keys, warps * kMaxLeaf,
+                                                                                (uint64_t)m << 40);
+  c.launches++;
+  const uint32_t rounds = (uint32_t)std::max<uint64_t>(1, 64 / cfg.seeds_per_lane);
+  cudaEvent_t e0, e1;
+  SHK_CUDA(cudaEventCreate(&e0));
+  SHK_CUDA(cudaEventCreate(&e1));
+  k->probe<<<blocks, cfg.warps * 32, 0, c.stream>>>(keys, m, rounds / 4 + 1, cnt);  // warm-up
+  SHK_CUDA(cudaMemsetAsync(cnt, 0, 8, c.stream));
+  SHK_CUDA(cudaEventRecord(e0, c.stream));
+  k->probe<<<blocks, cfg.warps * 32, 0, c.stream>>>(keys, m, rounds, cnt);
+  SHK_CUDA(cudaEventRecord(e1, c.stream));
+  c.launches += 2;
+  unsigned long long h = 0;
+  SHK_CUDA(cudaMemcpyAsync(&h, cnt, 8, cudaMemcpyDeviceToHost, c.stream));
+  SHK_CUDA(cudaStreamSynchronize(c.stream));
+  float ms = 0;
+  SHK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *evals_per_s = ms > 0 ? (double)h * m / (ms * 1e-3) : 0;
+  return SHK_OK;
+}
+
+shk_status tuned_leaf_cfg(Ctx& c, uint32_t m, LeafCfg* out) {
+  const uint32_t bin = m <= 16 ? 0 : (m <= 32 ? 1 : (m <= 48 ? 2 : 3));
+  const uint32_t rep = (bin + 1) * 16;
+  if (c.device < 0 || c.device >= 64) return fail(SHK_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  TuneSlot& slot = g_tune[c.device][bin];
+  if (!slot.done) {
+    double best = -1;
+    LeafCfg best_cfg = slot.cfg;
+    for (int i = 0; i < kNumLeafCfg; i++) {
+      double r = 0;
+      SHK_TRY(probe_leaf_cfg(c, kLeafTable[i].cfg, rep, &r));
+      if (r > best) {
+        best = r;
+        best_cfg = kLeafTable[i].cfg;
+      }
+    }
+    best_cfg.passes = default_passes(rep);
+    slot.cfg = best_cfg;
+    slot.evals_per_s = best;
+    slot.done = true;
   }
+  *out = slot.cfg;
+  out->passes = default_passes(m);
+  return SHK_OK;
 }
 
 // ---------------------------------------------------------------------------

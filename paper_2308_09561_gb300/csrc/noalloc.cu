@@ -97,7 +97,7 @@ extern "C" shk_status shk_leaf_search_noalloc(const uint64_t* leaf_keys, const u
     SHK_CUDA(cudaGetLastError());
     SHK_CUDA(cudaMemsetAsync(seeds_out, 0xFF, (size_t)n_leaves * 8, st));
     LeafSearchArgs a{d, n_leaves, leaf_keys, seed_start, (unsigned long long*)seeds_out, err,
-                     counter, 4, 8};
+                     counter, LeafCfg{4, 8, 2, 8}};
     SHK_TRY(launch_leaf_persistent_state(c, a, state));
     SHK_TRY(launch_orient(c, d, n_leaves, leaf_keys, (unsigned long long*)seeds_out, nullptr,
                           nullptr, f_out, err));

@@ -232,3 +232,48 @@ def test_million_keys_leaf48_sampled(pkg, orc):
     r_or = orc.query(blob, lo[samp], hi[samp])
     assert np.array_equal(r_or, ranks.cpu().numpy().view(np.uint64)[samp])
     m.close()
+
+
+@pytest.mark.parametrize("ci", range(10))
+def test_every_leaf_kernel_configuration_gives_the_same_build(pkg, orc, ci):
+    cfgs = pkg.shk_leaf_configs()
+    assert len(cfgs) == 10
+    U, W, R = cfgs[ci]
+    keys = inp.distinct_u64(6000, 77)
+    want = orc.build_mphf(keys, n=28, b=700)
+    for sched in (0, 1):
+        m = pkg.shk_build(_dev(keys), 28, 700, seeds_per_lane=U, warps_per_block=W, key_unroll=R,
+                          chunk_passes=3, sched=sched)
+        assert m.stats()["leaf_cfg"] == [U, W, R, 3]
+        assert m.serialize() == want
+
+
+def test_autotuner_picks_a_supported_configuration(pkg):
+    cfgs = pkg.shk_leaf_configs()
+    for m in (8, 24, 40, 64):
+        r = pkg.shk_leaf_tune(m)
+        assert (r["seeds_per_lane"], r["warps_per_block"], r["key_unroll"]) in cfgs
+        assert r["passes"] >= 1 and r["evals_per_s"] > 0
+    keys = inp.distinct_u64(3000, 78)
+    st = pkg.shk_build(_dev(keys), 40, 1000).stats()
+    r = pkg.shk_leaf_tune(40)
+    assert st["leaf_cfg"][:3] == [r["seeds_per_lane"], r["warps_per_block"], r["key_unroll"]]
+
+
+def test_leaf_search_graph_replay_reads_new_contents(pkg, orc):
+    import torch
+
+    keys1, offs = inp.leaf_instances(700, 61, 2, 40)
+    keys2 = inp.splitmix64_stream(62, keys1.size)
+    dk = _dev(keys1)
+    off = torch.from_numpy(offs.view(np.int32)).cuda()
+    seeds = torch.empty(700, dtype=torch.int64, device="cuda")
+    fm = torch.empty(700, dtype=torch.int64, device="cuda")
+    r0 = pkg.shk_leaf_graph_replays()
+    for keys in (keys1, keys2, keys1):
+        dk.copy_(_dev(keys))
+        pkg.shk_leaf_search(dk, off, 0, seeds_out=seeds, f_out=fm)
+        want_s, want_f = orc.leaf_search_batch(keys, offs, 0)
+        assert np.array_equal(seeds.cpu().numpy().view(np.uint64), want_s)
+        assert np.array_equal(fm.cpu().numpy().view(np.uint64), want_f)
+    assert pkg.shk_leaf_graph_replays() == r0 + 3
