@@ -27,11 +27,12 @@ sys.path.insert(0, ROOT)
 N_KEYS, LEAF, BUCKET, KEY_SEED = 1_000_000, 48, 2000, 2
 WORKLOAD = "mphf_build_1M_u64_keys_leaf48_bucket2000"
 METRIC = "MPHF build keys/s (1M u64 keys, leaf 48, bucket 2000), leaf seeds tested/s, % integer-issue roofline"
-# integer lane-operations of one key-seed evaluation of the leaf hash + filter
-# (x^c: 2, 64-bit multiply: 3, two range reductions: 2, h1 adjust: 2, two
-# candidate bits into a 64-bit mask held as two words: 8)
-OPS_PER_EVAL_WIDE = 17
-OPS_PER_EVAL_NARROW = 12
+# integer lane-operations of one key-seed evaluation of the leaf hash + filter:
+# xor 1, multiply-add 1, widening multiply by m 1, multiply-high by m-1 1,
+# h1 adjust 2 (compare, add), two candidate bits into the mask: 8 when the mask
+# is two 32-bit words (2 subtracts, 4 shifts, 2 ors; m > 32), 3 for m <= 32
+OPS_PER_EVAL_WIDE = 14
+OPS_PER_EVAL_NARROW = 9
 
 
 def _peaks():

@@ -60,10 +60,9 @@ enum { ORC_KEYS_U64 = 0, ORC_KEYS_STR = 1, ORC_KEYS_FP128 = 2 };
 #define ORC_HEADER_WORDS 16u
 #define ORC_MAGIC 0x31303053524B4853ull /* "SHKRS001" */
 
-/* Format constants: salts and the leaf multiplier (hex digits of pi). */
+/* Format constants: salts (hex digits of pi). */
 #define FP_HI_SALT 0x243F6A8885A308D3ull
 #define LEAF_SALT 0x13198A2E03707344ull
-#define LEAF_MUL 0x452821E638D01377ull
 #define SPLIT_SALT 0xBE5466CF34E90C6Cull
 #define RET_SALT 0xC0AC29B7C97C50DDull
 #define RET_SALT2 0x3F84D5B5B5470917ull
@@ -214,16 +213,20 @@ uint32_t orc_rice_k_leaf(uint32_t m) { return m >= 2 && m <= 64 ? K_LEAF[m] : 0;
 /* ------------------------------------------------------------------------ */
 /* Leaf hash (Sec. 3: key x gets candidate cells h_{s,0}(x), h_{s,1}(x) in   */
 /* [m]; footnote in Sec. 4: self-loops are avoided).  Reading:               */
-/*   c = mix(LEAF_SALT + s); p = (x ^ c) * LEAF_MUL mod 2^64;                 */
-/*   h0 = floor(hi32(p) * m / 2^32); t = floor(lo32(p) * (m-1) / 2^32);        */
-/*   h1 = t + (t >= h0)  -- uniform over the cells other than h0.             */
+/*   c = mix(LEAF_SALT + s);                                                  */
+/*   a = (lo32(x) ^ lo32(c)) * (hi32(x) | 1) + hi32(c)  mod 2^32;              */
+/*   h0 = floor(a * m / 2^32);  r = a * m mod 2^32;                            */
+/*   t = floor(r * (m-1) / 2^32);  h1 = t + (t >= h0)                          */
+/* -- h0 uniform over [m], h1 uniform over the other m-1 cells.               */
 /* ------------------------------------------------------------------------ */
 void orc_leaf_hash(uint64_t x, uint64_t seed, uint32_t m, uint32_t* h0, uint32_t* h1) {
   uint64_t c = orc_mix64(LEAF_SALT + seed);
-  uint64_t p = (x ^ c) * LEAF_MUL;
-  uint32_t a = (uint32_t)(p >> 32), b = (uint32_t)p;
-  uint32_t u = (uint32_t)(((uint64_t)a * m) >> 32);
-  uint32_t t = (uint32_t)(((uint64_t)b * (m - 1)) >> 32);
+  uint32_t y = (uint32_t)x ^ (uint32_t)c;
+  uint32_t mult = (uint32_t)(x >> 32) | 1u;
+  uint32_t a = y * mult + (uint32_t)(c >> 32);
+  uint64_t w = (uint64_t)a * m;
+  uint32_t u = (uint32_t)(w >> 32);
+  uint32_t t = (uint32_t)(((uint64_t)(uint32_t)w * (m - 1)) >> 32);
   *h0 = u;
   *h1 = t + (t >= u ? 1u : 0u);
 }

@@ -105,22 +105,26 @@ __device__ uint64_t search_seeds(WarpScratch* ws, uint32_t m, uint64_t s0, uint3
     const uint64_t base = s0 + (uint64_t)pass * (32u * U);
     if (best != nullptr && base >= read_uniform(best)) return ~0ull;
     *done += 32u * U;
-    uint64_t c[U];
-    uint32_t mlo[U], mhi[U];
+    uint32_t cl[U], ch[U], mlo[U], mhi[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      c[u] = mix64(kLeafSalt + base + (uint64_t)(u * 32) + lane);
+      const uint64_t c = mix64(kLeafSalt + base + (uint64_t)(u * 32) + lane);
+      cl[u] = (uint32_t)c;
+      ch[u] = (uint32_t)(c >> 32);
       mlo[u] = 0;
       mhi[u] = 0;
     }
 #pragma unroll UNROLL
     for (uint32_t i = 0; i < m; i++) {
+      // ws->x holds (lo32(x), hi32(x) | 1): the key's xor input and multiplier
       const uint64_t x = ws->x[i];
+      const uint32_t xl = (uint32_t)x, mult = (uint32_t)(x >> 32);
 #pragma unroll
       for (int u = 0; u < U; u++) {
-        const uint64_t p = (x ^ c[u]) * kLeafMul;
-        const uint32_t h0 = __umulhi((uint32_t)(p >> 32), m);
-        const uint32_t t = __umulhi((uint32_t)p, m1);
+        const uint32_t a = (xl ^ cl[u]) * mult + ch[u];
+        const uint64_t w = (uint64_t)a * m;
+        const uint32_t h0 = (uint32_t)(w >> 32);
+        const uint32_t t = __umulhi((uint32_t)w, m1);
         const uint32_t h1 = t + (t >= h0 ? 1u : 0u);
         mlo[u] |= bit32(h0) | bit32(h1);
         if (WIDE) mhi[u] |= bit32(h0 - 32u) | bit32(h1 - 32u);
@@ -158,9 +162,13 @@ __device__ __forceinline__ uint64_t search_dispatch(WarpScratch* ws, uint32_t m,
                 : search_seeds<U, UNROLL, false>(ws, m, s0, passes, best, done);
 }
 
+// Keys of a leaf into shared memory with the multiplier's low bit set
+// (leaf_cells gives the same cells for x and for x with that bit set).
+__device__ __forceinline__ uint64_t leaf_input(uint64_t x) { return x | (1ull << 32); }
+
 __device__ __forceinline__ void load_leaf(WarpScratch* ws, const LeafDesc& d, const uint64_t* x) {
   const uint32_t lane = threadIdx.x & 31;
-  for (uint32_t i = lane; i < d.m; i += 32) ws->x[i] = x[d.key_off + i];
+  for (uint32_t i = lane; i < d.m; i += 32) ws->x[i] = leaf_input(x[d.key_off + i]);
   __syncwarp();
 }
 
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(WARPS * 32)
   const uint32_t lane = threadIdx.x & 31;
   WarpScratch* ws = &scratch[threadIdx.x >> 5];
   const uint32_t gw = blockIdx.x * WARPS + (threadIdx.x >> 5);
-  for (uint32_t i = lane; i < m; i += 32) ws->x[i] = keys[(uint64_t)gw * kMaxLeaf + i];
+  for (uint32_t i = lane; i < m; i += 32) ws->x[i] = leaf_input(keys[(uint64_t)gw * kMaxLeaf + i]);
   __syncwarp();
   uint32_t done = 0;
   for (uint32_t r = 0; r < rounds; r++)

@@ -19,7 +19,6 @@ namespace shk {
 // ---------------------------------------------------------------------------
 constexpr uint64_t kFpHiSalt = 0x243F6A8885A308D3ull;
 constexpr uint64_t kLeafSalt = 0x13198A2E03707344ull;
-constexpr uint64_t kLeafMul = 0x452821E638D01377ull;
 constexpr uint64_t kSplitSalt = 0xBE5466CF34E90C6Cull;
 constexpr uint64_t kRetSalt = 0xC0AC29B7C97C50DDull;
 constexpr uint64_t kRetSalt2 = 0x3F84D5B5B5470917ull;
@@ -119,12 +118,15 @@ __host__ __device__ inline uint32_t rice_k_split(uint32_t m, uint32_t n) {
 
 // Leaf hash (Sec. 3; self-loops avoided): the two candidate cells of key x
 // under seed constant c = mix(kLeafSalt + s) in a leaf of m >= 2 cells.
+// a = (lo32(x) ^ lo32(c)) * (hi32(x) | 1) + hi32(c) mod 2^32; a * m gives h0
+// (high word) and, from its low word r, t = floor(r (m-1) / 2^32) and
+// h1 = t + (t >= h0).
 __host__ __device__ __forceinline__ void leaf_cells(uint64_t x, uint64_t c, uint32_t m,
                                                     uint32_t* h0, uint32_t* h1) {
-  const uint64_t p = (x ^ c) * kLeafMul;
-  const uint32_t a = (uint32_t)(p >> 32), b = (uint32_t)p;
-  const uint32_t u = (uint32_t)(((uint64_t)a * m) >> 32);
-  const uint32_t t = (uint32_t)(((uint64_t)b * (m - 1)) >> 32);
+  const uint32_t a = ((uint32_t)x ^ (uint32_t)c) * ((uint32_t)(x >> 32) | 1u) + (uint32_t)(c >> 32);
+  const uint64_t w = (uint64_t)a * m;
+  const uint32_t u = (uint32_t)(w >> 32);
+  const uint32_t t = (uint32_t)(((uint64_t)(uint32_t)w * (m - 1)) >> 32);
   *h0 = u;
   *h1 = t + (t >= u ? 1u : 0u);
 }
