@@ -4,10 +4,10 @@
  * The library builds minimal perfect hash functions (MPHFs): bijections from a
  * set of N distinct keys onto [0, N) (paper Sec. 1), with the ShockHash-RS
  * construction: keys hashed to buckets and split recursively (RecSplit, Sec. 2;
- * fanouts Sec. 5), each leaf solved by the ShockHash seed search (Sec. 3, Eq.
+ * fanouts Sec. 6), each leaf solved by the ShockHash seed search (Sec. 4, Eq.
  * ShockHash: the smallest seed whose 2-choice graph is a pseudoforest, with the
- * bit-mask filter of Sec. 3), the orientation bits of all keys stored in one
- * 1-bit retrieval structure (Sec. 2 Retrieval, Sec. 5).  Every step runs in CUDA
+ * bit-mask filter of Sec. 4), the orientation bits of all keys stored in one
+ * 1-bit retrieval structure (Sec. 2 Retrieval, Sec. 6).  Every step runs in CUDA
  * kernels on the calling device; the result is bit-identical to the format
  * defined by the project (version SHKRS001).
  *
@@ -106,7 +106,7 @@ typedef struct {
 
 typedef struct shk_mphf shk_mphf;
 
-/* shk_build -- construct an MPHF over keys (paper Sec. 5, ShockHash-RS).
+/* shk_build -- construct an MPHF over keys (paper Sec. 6, ShockHash-RS).
  *   keys:   borrowed; host or device buffers (keys->on_device).
  *   opts:   leaf_size n in [2, 64]; bucket_size b in [n, 4096].
  *   out:    receives a new object owned by the caller (shk_free).
@@ -119,7 +119,7 @@ shk_status shk_build(const shk_keys* keys, const shk_build_opts* opts, void* cud
 /* shk_build_stats -- statistics of the build that produced mphf. */
 shk_status shk_build_stats(const shk_mphf* mphf, shk_stats* out);
 
-/* shk_query -- ranks of keys (paper Sec. 1: x -> p_{g(x)} + h_{g(x)}(x); Sec. 3:
+/* shk_query -- ranks of keys (paper Sec. 1: x -> p_{g(x)} + h_{g(x)}(x); Sec. 4:
  * the leaf part is h_{s,f(x)}(x) with f(x) from the retrieval structure).
  *   ranks_out: uint64_t[keys->n_keys], device memory if out_on_device, else host.
  * For keys of the build set the ranks are a permutation of [0, N); for other
@@ -146,7 +146,7 @@ void shk_free(shk_mphf* mphf);
 const char* shk_last_error(void);
 
 /* shk_leaf_search -- batched ShockHash leaf search over independent leaves
- * (paper Sec. 3: for each leaf the smallest seed >= seed_start whose graph
+ * (paper Sec. 4: for each leaf the smallest seed >= seed_start whose graph
  * ([m], {{h0(x), h1(x)}}) is a pseudoforest, found with the bit-mask filter
  * and a union-find test of survivors; f = the lexicographically smallest
  * 1-orientation).

@@ -12,21 +12,21 @@
  *
  * Where the paper fixes the result it is written out as that definition:
  *   - the leaf seed is the minimum seed whose 2-choice graph admits a
- *     1-orientation (Sec. 3, Eq. ShockHash), tested as "every connected
+ *     1-orientation (Sec. 4, Eq. ShockHash), tested as "every connected
  *     component has at most as many edges as nodes" (Sec. 2, Pseudoforests);
  *   - the bit-mask filter is "every table cell is a candidate of some key"
- *     (Sec. 3, Filter by Bit Mask), a necessary condition only;
+ *     (Sec. 4, Filter by Bit Mask), a necessary condition only;
  *   - a split seed is the minimum seed giving the prescribed part sizes
  *     (Sec. 2, RecSplit);
  *   - rank(x) = prefix(bucket) + offset of the leaf + h_{s,f(x)}(x)
- *     (Sec. 1 prefix-sum form; Sec. 3 query).
+ *     (Sec. 1 prefix-sum form; Sec. 4 query).
  * Where the paper is silent (hash functions, tree shape above the two lowest
  * levels, Rice parameters, bit order, Elias-Fano layout, the retrieval
  * structure, which of the 2^c orientations to keep) the code follows the
  * project's frozen format readings; each function names its reading.
  *
  * Pins (tests/test_oracle_*.py): brute force over all graphs for m <= 6,
- * exact coverage probability, Fig. 4 trial counts, brute-force orientation,
+ * exact coverage probability, Fig. 2 trial counts, brute-force orientation,
  * brute-force ribbon solutions, Rice/EF round trips, bijection of every build.
  * Parity unpinned: the fingerprint, split, leaf and retrieval hash *values*
  * (the paper defines no hash function); they are pinned only through the
@@ -71,7 +71,7 @@ enum { ORC_KEYS_U64 = 0, ORC_KEYS_STR = 1, ORC_KEYS_FP128 = 2 };
 
 /* Rice parameter of a leaf of m keys: floor(log2(ln2 * mu(m))) with mu(m) the
  * mean number of seeds tried, mu ~ 0.8 (e/2)^m e / sqrt(pi m) (the paper's
- * trial bound of Thm. shockHashConstruction divided by sqrt(m), as Sec. 7.1
+ * trial bound of Thm. shockHashConstruction divided by sqrt(m), as Sec. 8.1
  * observes).  Frozen as a literal format table; index 0 and 1 unused. */
 static const uint8_t K_LEAF[65] = {
     0,  0,  0,  0,  0,  0,  1,  1,  1,  2,  2,  2,  3,  3,  4,  4,  4,
@@ -92,7 +92,7 @@ uint64_t orc_mix64(uint64_t z) {
 static uint64_t rotl64(uint64_t v, unsigned r) { return (v << r) | (v >> (64 - r)); }
 
 /* ------------------------------------------------------------------------ */
-/* Master hash code (Sec. 7: every key is first reduced to one high-quality  */
+/* Master hash code (Sec. 8: every key is first reduced to one high-quality  */
 /* hash; all later hashes are functions of it).  128-bit fingerprint.        */
 /* Reading: u64 key k -> (lo, hi) = (mix(k), mix(k ^ FP_HI_SALT)); mix is a   */
 /* bijection, so distinct integer keys never share lo.                        */
@@ -130,7 +130,7 @@ uint64_t orc_bucket(uint64_t hi, uint64_t B) { return (uint64_t)(((u128)hi * B) 
 
 /* ------------------------------------------------------------------------ */
 /* Splitting-tree shape (Sec. 2 RecSplit: the shape depends only on the      */
-/* node size; Sec. 5 Fanouts: lowest split level 4, next 3 for n > 24, all 2 */
+/* node size; Sec. 6 Fanouts: lowest split level 4, next 3 for n > 24, all 2 */
 /* for n <= 24).  Reading for the remaining levels: binary splits whose left */
 /* part is a multiple of the second-level size.                              */
 /* Returns 0 for a leaf, else 1 with unit and fanout set; part j < fanout-1  */
@@ -211,8 +211,8 @@ uint32_t orc_rice_k_split(uint32_t m, uint32_t n) {
 uint32_t orc_rice_k_leaf(uint32_t m) { return m >= 2 && m <= 64 ? K_LEAF[m] : 0; }
 
 /* ------------------------------------------------------------------------ */
-/* Leaf hash (Sec. 3: key x gets candidate cells h_{s,0}(x), h_{s,1}(x) in   */
-/* [m]; footnote in Sec. 4: self-loops are avoided).  Reading:               */
+/* Leaf hash (Sec. 4: key x gets candidate cells h_{s,0}(x), h_{s,1}(x) in   */
+/* [m]; footnote in Sec. 5: self-loops are avoided).  Reading:               */
 /*   c = mix(LEAF_SALT + s);                                                  */
 /*   a = (lo32(x) ^ lo32(c)) * (hi32(x) | 1) + hi32(c)  mod 2^32;              */
 /*   h0 = floor(a * m / 2^32);  r = a * m mod 2^32;                            */
@@ -258,7 +258,7 @@ int orc_is_pseudoforest(const uint32_t* h0, const uint32_t* h1, uint32_t m) {
   return 1;
 }
 
-/* Bit-mask filter (Sec. 3, Filter by Bit Mask): every cell is a candidate of
+/* Bit-mask filter (Sec. 4, Filter by Bit Mask): every cell is a candidate of
  * some key. */
 int orc_covers_all(const uint32_t* h0, const uint32_t* h1, uint32_t m) {
   uint64_t mask = 0;
@@ -278,7 +278,7 @@ void orc_pf_batch(const uint32_t* h0, const uint32_t* h1, uint64_t count, uint32
   }
 }
 
-/* Leaf seed (Sec. 3, Eq. ShockHash): the smallest s >= start such that some
+/* Leaf seed (Sec. 4, Eq. ShockHash): the smallest s >= start such that some
  * f makes x -> h_{s,f(x)}(x) a bijection onto [m], i.e. the graph
  * ([m], {{h0(x), h1(x)}}) is a pseudoforest.  The filter only skips seeds
  * that cannot pass; use_filter = 0 tests every seed in full. */
@@ -315,7 +315,7 @@ void orc_leaf_seed_stats(const uint64_t* x, uint32_t m, uint64_t s0, uint64_t co
 }
 
 /* ------------------------------------------------------------------------ */
-/* Orientation.  A pseudoforest has 2^c 1-orientations (Sec. 4, Eq.          */
+/* Orientation.  A pseudoforest has 2^c 1-orientations (Sec. 5, Eq.          */
 /* orientations-cycles).  Reading: keep the lexicographically smallest f     */
 /* (key 0 first, f = 0 meaning cell h0).  Written as the definition: fix     */
 /* f(0), f(1), ... greedily to 0 whenever a bijection still exists, checked  */
@@ -464,7 +464,7 @@ static uint64_t get_bits(const uint64_t* w, uint64_t p, uint32_t nbits) {
   return v;
 }
 
-/* Golomb-Rice code (Sec. 3: the seed is stored with Golomb-Rice codes).
+/* Golomb-Rice code (Sec. 4: the seed is stored with Golomb-Rice codes).
  * Reading: the k low bits of s LSB-first, then q = s >> k one-bits and a
  * terminating zero-bit. */
 static int rice_put(bitvec_t* bv, uint64_t s, uint32_t k) {
@@ -619,7 +619,7 @@ static void ef_decode_all(const uint64_t* low, const uint64_t* high, uint64_t hb
 }
 
 /* ------------------------------------------------------------------------ */
-/* 1-bit retrieval (Sec. 2 Retrieval; Sec. 5: all f bits go into one          */
+/* 1-bit retrieval (Sec. 2 Retrieval; Sec. 6: all f bits go into one          */
 /* retrieval structure).  Reading: a standard ribbon, width 64, sharded by   */
 /* runs of shard_buckets buckets.  Shard slots m = keys + ceil(keys * eps /  */
 /* 2^16) + 63 (0 for an empty shard).  Key equation with shard seed r:        */
@@ -915,7 +915,7 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
-/* Query (Sec. 1: x -> p_{g(x)} + h_{g(x)}(x); Sec. 3: retrieve f(x), return */
+/* Query (Sec. 1: x -> p_{g(x)} + h_{g(x)}(x); Sec. 4: retrieve f(x), return */
 /* h_{s,f(x)}(x)).  Decodes the tree from the bucket's Rice stream.          */
 /* ------------------------------------------------------------------------ */
 typedef struct {

@@ -1,4 +1,4 @@
-// encode.cu -- Golomb-Rice code of all seeds (paper Sec. 3: the seed is stored
+// encode.cu -- Golomb-Rice code of all seeds (paper Sec. 4: the seed is stored
 // with Golomb-Rice codes) and the Elias-Fano bucket index (Sec. 1: prefix sums
 // of bucket sizes).  Bit vectors are LSB-first: bit p is bit p%64 of word p/64;
 // concurrent writers only ever OR bits into zeroed words.

@@ -1,7 +1,7 @@
-// leaf.cu -- ShockHash leaf seed search (paper Sec. 3, Eq. ShockHash) with the
-// bit-mask filter (Sec. 3, Filter by Bit Mask), the union-find pseudoforest test
+// leaf.cu -- ShockHash leaf seed search (paper Sec. 4, Eq. ShockHash) with the
+// bit-mask filter (Sec. 4, Filter by Bit Mask), the union-find pseudoforest test
 // of filter survivors (App. A.1) and the orientation of the winning graph
-// (Sec. 4, Eq. orientations-cycles).
+// (Sec. 5, Eq. orientations-cycles).
 //
 // Warp design: the 32 lanes of a warp test consecutive seeds of one leaf; each
 // lane carries U seeds at once, so every key read from shared memory (a

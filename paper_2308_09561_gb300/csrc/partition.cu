@@ -1,6 +1,6 @@
 // partition.cu -- master hash, bucket histogram, prefix sums, radix
 // partition into buckets and the in-bucket sort (paper Sec. 2 RecSplit: keys
-// are hashed to buckets; Sec. 7: every key is first reduced to a master hash).
+// are hashed to buckets; Sec. 8: every key is first reduced to a master hash).
 #include "kernels.cuh"
 
 namespace shk {

@@ -1,4 +1,4 @@
-// query.cu -- rank of a key (paper Sec. 1: x -> p_{g(x)} + h_{g(x)}(x); Sec. 3:
+// query.cu -- rank of a key (paper Sec. 1: x -> p_{g(x)} + h_{g(x)}(x); Sec. 4:
 // a ShockHash leaf returns h_{s,f(x)}(x) with f(x) from the retrieval
 // structure).  One thread per key: bucket from the fingerprint, tree descent
 // by decoding the bucket's Rice stream, leaf cell, retrieval parity.

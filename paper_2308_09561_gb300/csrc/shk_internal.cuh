@@ -1,8 +1,8 @@
 // shk_internal.cuh -- shared definitions of the GB300 ShockHash-RS library.
 //
 // Format constants and the arithmetic of the SHKRS001 format as used by the
-// kernels.  The definitions follow the paper (ShockHash, Sec. 3; ShockHash-RS,
-// Sec. 5) and the project's frozen readings for what the paper leaves open.
+// kernels.  The definitions follow the paper (ShockHash, Sec. 4; ShockHash-RS,
+// Sec. 6) and the project's frozen readings for what the paper leaves open.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -44,7 +44,7 @@ constexpr uint32_t kErrOrient = 1u << 5;
 
 // Rice parameter of a leaf of m keys (frozen literal table of the format):
 // floor(log2(ln2 * 0.8 (e/2)^m e / sqrt(pi m))), the trial bound of the
-// paper's Thm. shockHashConstruction divided by sqrt(m) (Sec. 7.1).
+// paper's Thm. shockHashConstruction divided by sqrt(m) (Sec. 8.1).
 __host__ __device__ inline uint32_t rice_k_leaf(uint32_t m) {
   constexpr uint8_t t[65] = {0,  0,  0,  0,  0,  0,  1,  1,  1,  2,  2,  2,  3,  3,  4,  4,  4,
                              5,  5,  6,  6,  6,  7,  7,  8,  8,  8,  9,  9,  10, 10, 11, 11, 11,
@@ -71,7 +71,7 @@ __host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
 #endif
 }
 
-// Tree shape (RecSplit, Sec. 2; fanouts Sec. 5): a node of m keys is a leaf
+// Tree shape (RecSplit, Sec. 2; fanouts Sec. 6): a node of m keys is a leaf
 // when m <= n; otherwise its parts are (fanout - 1) x unit plus the remainder.
 struct SplitShape {
   uint32_t unit, fanout;
@@ -116,7 +116,7 @@ __host__ __device__ inline uint32_t rice_k_split(uint32_t m, uint32_t n) {
   return lg / 2;
 }
 
-// Leaf hash (Sec. 3; self-loops avoided): the two candidate cells of key x
+// Leaf hash (Sec. 4; self-loops avoided): the two candidate cells of key x
 // under seed constant c = mix(kLeafSalt + s) in a leaf of m >= 2 cells.
 // a = (lo32(x) ^ lo32(c)) * (hi32(x) | 1) + hi32(c) mod 2^32; a * m gives h0
 // (high word) and, from its low word r, t = floor(r (m-1) / 2^32) and

@@ -1,6 +1,6 @@
 // tree.cu -- the RecSplit splitting tree of every bucket (paper Sec. 2: a
 // bucket is split recursively by searching splitting seeds; the shape depends
-// only on the node size; Sec. 5: fanouts of the two lowest levels).
+// only on the node size; Sec. 6: fanouts of the two lowest levels).
 #include "kernels.cuh"
 
 namespace shk {

@@ -8,7 +8,7 @@ The generator is the splitmix64 stream (Steele, Lea, Flood, OOPSLA 2014):
 state_i = seed + i * 0x9E3779B97F4A7C15, output_i = splitmix64-output(state_i),
 i = 1, 2, ...  Uniform doubles in [0, 1) take the top 53 bits.
 
-Workloads (stand-ins for the paper's random-string inputs, Sec. 7):
+Workloads (stand-ins for the paper's random-string inputs, Sec. 8):
   * ``distinct_u64(count, seed)``: the stream's outputs in order, repeats
     skipped, until ``count`` distinct 64-bit keys.
   * ``leaf_instances(count, seed)``: independent leaves with sizes

@@ -107,7 +107,7 @@ def test_format_sections_decode(orc):
 
 def test_every_key_retrieves_its_orientation(orc):
     """Sec. 2 Retrieval: the structure returns the stored f for every key;
-    the rank uses h_{s,f(x)}(x) of its leaf (Sec. 3)."""
+    the rank uses h_{s,f(x)}(x) of its leaf (Sec. 4)."""
     N, n, b = 4000, 16, 400
     keys = inp.distinct_u64(N, 21)
     blob = orc.build_mphf(keys, n=n, b=b)

@@ -48,7 +48,7 @@ def test_mixer_is_bijective_on_a_sample(orc):
 
 
 # --------------------------------------------------------------------------
-# pseudoforest test and filter: brute force over all graphs (Sec. 2, Sec. 3)
+# pseudoforest test and filter: brute force over all graphs (Sec. 2, Sec. 4)
 # --------------------------------------------------------------------------
 def _all_loopfree_graphs(m):
     pairs = [(a, b) for a in range(m) for b in range(m) if a != b]
@@ -58,7 +58,7 @@ def _all_loopfree_graphs(m):
 
 
 def _bijection_exists_bruteforce(h0, h1):
-    """Sec. 4: ori(f) = x -> h_{f(x)}(x) bijective; some f among all 2^m."""
+    """Sec. 5: ori(f) = x -> h_{f(x)}(x) bijective; some f among all 2^m."""
     count, m = h0.shape
     ok = np.zeros(count, bool)
     full = (1 << m) - 1
@@ -81,7 +81,7 @@ def test_pseudoforest_equals_orientability_all_graphs(orc, m, p_exact):
     brute = _bijection_exists_bruteforce(h0, h1)
     assert np.array_equal(pf, brute)
     assert Fraction(int(pf.sum()), pf.size) == p_exact
-    # the filter is necessary (Sec. 3, Filter by Bit Mask)
+    # the filter is necessary (Sec. 4, Filter by Bit Mask)
     assert not np.any(pf & ~cov)
 
 
@@ -149,7 +149,7 @@ def test_pseudoforest_random_graphs_agree_with_bruteforce(orc):
 
 
 # --------------------------------------------------------------------------
-# leaf seed: minimum (Eq. ShockHash) and trial counts (Fig. 4)
+# leaf seed: minimum (Eq. ShockHash) and trial counts (Fig. 2)
 # --------------------------------------------------------------------------
 def test_leaf_seed_is_minimum_and_filter_changes_nothing(orc):
     for m in (2, 3, 5, 8, 12, 16):
@@ -203,9 +203,9 @@ def test_trials_match_uniform_random_graphs(orc, m):
     assert abs(mean - mu) < 4.5 * math.hypot(se, se_mu)
 
 
-@pytest.mark.parametrize("row", _golden_rows("fig4_shockhash.txt")[:10])
+@pytest.mark.parametrize("row", _golden_rows("fig2_hash_function_evals.txt")[:10])
 def test_trials_against_fig4(orc, row):
-    """Fig. 4 (left): ShockHash's average successful seed.  The paper's hash
+    """Fig. 2 (left): ShockHash's average successful seed.  The paper's hash
     leaves self-loops out in an unstated way and its series sits 5-11 %
     above the ideal loop-free model; ours must lie within 15 % below it and
     never above it by more than the statistical error.  Also the upper bound
@@ -221,9 +221,9 @@ def test_trials_against_fig4(orc, row):
     assert mean <= (math.e / 2) ** m * math.e / math.sqrt(math.pi)
 
 
-@pytest.mark.parametrize("row", [r for r in _golden_rows("fig4_shockhash.txt") if int(r[0]) in (16, 20, 24)])
+@pytest.mark.parametrize("row", [r for r in _golden_rows("fig2_hash_function_evals.txt") if int(r[0]) in (16, 20, 24)])
 def test_idealized_space_overhead_against_fig4(orc, row):
-    """Fig. 4 (right): log2(avg seed) + n - log2(n^n/n!) bits."""
+    """Fig. 2 (right): log2(avg seed) + n - log2(n^n/n!) bits."""
     m, fig_overhead = int(row[0]), float(row[2])
     L = 6000
     keys = inp.splitmix64_stream(5000 + m, L * m)
@@ -271,7 +271,7 @@ def test_orientation_is_lexicographic_minimum_and_count(orc, m):
 
 
 # --------------------------------------------------------------------------
-# splitting tree (Sec. 2 RecSplit, Sec. 5 Fanouts)
+# splitting tree (Sec. 2 RecSplit, Sec. 6 Fanouts)
 # --------------------------------------------------------------------------
 def _leaves(orc, m, n):
     sh = orc.split_shape(m, n)
@@ -365,8 +365,8 @@ def test_rice_parameters():
     assert oracle.rice_k_split(2000, 64) == 5
     assert oracle.rice_k_split(256, 64) == 11
     assert oracle.rice_k_leaf(64) == 25 and oracle.rice_k_leaf(32) == 11
-    # the leaf table follows log2(ln2 * trials) of Fig. 4 within one unit
-    for r in _golden_rows("fig4_shockhash.txt"):
+    # the leaf table follows log2(ln2 * trials) of Fig. 2 within one unit
+    for r in _golden_rows("fig2_hash_function_evals.txt"):
         m, trials = int(r[0]), float(r[1])
         assert abs(oracle.rice_k_leaf(m) - math.log2(math.log(2) * trials)) < 1.2
 
