@@ -352,6 +352,82 @@ def run_leafbatch(args):
     return 0
 
 
+def run_serve(args):
+    """Served builds: a Poisson stream of MPHF build requests (uniform u64
+    keys, sizes log-uniform in [1e3, 3e5], leaf size 48 or 58 by coin, bucket
+    2000, stream seed 5, request i from sub-seed 5 + 7919 i) into one server
+    with 4 builds in flight.  The arrival rate is set for ~80 % offered load
+    from a calibration build of each leaf size.  Reports p50/p99 build latency
+    (submit to finish) and aggregate keys/s."""
+    import torch
+
+    import paper_2308_09561_gb300 as pkg
+    import shk_inputs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pkg.load_library()
+    R = args.requests
+    u = shk_inputs.uniform01(5 + 1000 * rank, 3 * R)
+    sizes = np.floor(10 ** (3 + np.log10(300) * u[0::3])).astype(np.int64)
+    leafs = np.where(u[1::3] < 0.5, 48, 58)
+    reqs = [(shk_inputs.distinct_u64(int(sz), 5 + 7919 * i + 1000003 * rank), int(n))
+            for i, (sz, n) in enumerate(zip(sizes, leafs))]
+    # calibration: seconds per key of a build at each leaf size
+    per_key = {}
+    for n in (48, 58):
+        k = shk_inputs.distinct_u64(60000, 77 + n)
+        pkg.shk_build(k, n, BUCKET).close()  # tuning / warm-up
+        t = time.perf_counter()
+        pkg.shk_build(k, n, BUCKET).close()
+        per_key[n] = (time.perf_counter() - t) / k.size
+    service = float(np.mean([k.size * per_key[n] for k, n in reqs]))
+    rate = 0.8 / service
+    gaps = -np.log(1.0 - shk_inputs.uniform01(55 + 1000 * rank, R)) / rate
+    srv = pkg.shk_server_create(0, 4)
+    pending, infos = {}, []
+    t0 = time.perf_counter()
+    arrivals = t0 + np.cumsum(gaps)
+    with ClockSampler(local) as clk:
+        for i, (keys, n) in enumerate(reqs):
+            while time.perf_counter() < arrivals[i]:
+                for rid in list(pending):
+                    m, info = pkg.shk_server_poll(srv, rid)
+                    if info["done"]:
+                        infos.append(info)
+                        pending.pop(rid)
+                        if m is not None:
+                            m.close()
+                time.sleep(0.0005)
+            pending[pkg.shk_server_submit(srv, keys, n, BUCKET)] = i
+        for rid in list(pending):
+            m, info = pkg.shk_server_wait(srv, rid)
+            infos.append(info)
+            if m is not None:
+                m.close()
+    st = pkg.shk_server_get_stats(srv)
+    pkg.shk_server_destroy(srv)
+    lat = np.array([(i["finish_ns"] - i["submit_ns"]) / 1e6 for i in infos])
+    ok = all(i["status"] == 0 for i in infos)
+    span = (max(i["finish_ns"] for i in infos) - min(i["submit_ns"] for i in infos)) / 1e9
+    total = int(sum(k.size for k, _ in reqs))
+    line = {"metric": "served MPHF builds: aggregate keys/s, p50/p99 latency", "value": total / span,
+            "unit": "keys/s", "n_gpus": ws, "steps": 1, "warmup": 2, "higher_is_better": True,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "served_builds_poisson", "requests": R, "sizes": "log-uniform [1e3, 3e5]",
+                       "leaf_sizes": [48, 58], "bucket_size": BUCKET, "offered_load": 0.8, "workers": 4},
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "all_ok": ok, "total_keys": total, "makespan_s": span,
+            "arrival_rate_per_s": rate, "calibration_s_per_key": per_key,
+            "peak_reserved_bytes": st["peak_in_use_bytes"]}
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,13 +438,16 @@ def main():
     ap.add_argument("--keys", type=int, default=N_KEYS, help="smaller key counts for profiling runs")
     ap.add_argument("--compare-per-bucket", action="store_true",
                     help="time the one-launch-per-bucket form on the whole workload (slow)")
-    ap.add_argument("--workload", default="build", choices=["build", "leafbatch"],
+    ap.add_argument("--requests", type=int, default=100, help="serve: number of requests")
+    ap.add_argument("--workload", default="build", choices=["build", "leafbatch", "serve"],
                     help="leafbatch: 65,536 independent leaves of 40..64 keys, one graph-replayed launch")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "leafbatch":
         return run_leafbatch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

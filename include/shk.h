@@ -198,6 +198,59 @@ uint32_t shk_leaf_configs(uint32_t* cfgs, uint32_t cap);
  * calls with unchanged pointers and sizes reuse the instantiated graph). */
 uint64_t shk_leaf_graph_replays(void);
 
+/* ---- Serving: a request loop over builds of different sizes ----------------
+ * A server owns a queue of build requests and a pool of workers, each with its
+ * own CUDA stream on the device current at creation.  A request is admitted
+ * (first in, first out) as soon as a worker is free and its estimated device
+ * footprint fits in what the budget leaves (a request larger than the whole
+ * budget runs alone).  Admitted builds run concurrently, so the kernels of
+ * different requests overlap on the GPU, and requests arriving while others
+ * run are admitted as slots and memory free up.  Each result is the same MPHF
+ * that shk_build returns for the same keys and options. */
+typedef struct shk_server shk_server;
+
+typedef struct {
+  int32_t done;               /* 1 when finished (successfully or not)      */
+  int32_t status;             /* the build's status once done               */
+  uint64_t n_keys;
+  uint64_t footprint_bytes;   /* device memory reserved by admission        */
+  uint64_t submit_ns, start_ns, finish_ns; /* steady-clock timestamps       */
+} shk_request_info;
+
+typedef struct {
+  uint64_t submitted, completed, queued, running;
+  uint64_t budget_bytes, in_use_bytes, peak_in_use_bytes;
+  uint32_t workers;
+} shk_server_stats;
+
+/* shk_server_create -- hbm_budget_bytes: device memory the server may reserve
+ * for running builds (0 = 80 % of the free memory); workers: builds in flight
+ * (0 = 4). */
+shk_status shk_server_create(uint64_t hbm_budget_bytes, uint32_t workers, shk_server** out);
+
+/* shk_server_submit -- queue a build.  keys are copied before the call returns
+ * (host or device buffers); opts as for shk_build.  *req_id identifies it. */
+shk_status shk_server_submit(shk_server* srv, const shk_keys* keys, const shk_build_opts* opts,
+                             uint64_t* req_id);
+
+/* shk_server_poll -- non-blocking.  While the request runs or waits, *out is
+ * NULL and info->done is 0.  Once done, *out receives the MPHF (owned by the
+ * caller; NULL if the build failed, with info->status its error) and the
+ * request is forgotten.  SHK_EINVAL for an unknown request id. */
+shk_status shk_server_poll(shk_server* srv, uint64_t req_id, shk_mphf** out,
+                           shk_request_info* info);
+
+/* shk_server_wait -- as shk_server_poll, blocking until the request is done. */
+shk_status shk_server_wait(shk_server* srv, uint64_t req_id, shk_mphf** out,
+                           shk_request_info* info);
+
+/* shk_server_get_stats -- counters and the device-memory reservation. */
+shk_status shk_server_get_stats(shk_server* srv, shk_server_stats* out);
+
+/* shk_server_destroy -- finish running builds, drop queued ones, free results
+ * never polled.  NULL is ignored. */
+void shk_server_destroy(shk_server* srv);
+
 /* shk_version -- format version string ("SHKRS001"). */
 const char* shk_version(void);
 

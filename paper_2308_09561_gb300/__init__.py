@@ -26,7 +26,9 @@ SHK_SCHED_PERSISTENT, SHK_SCHED_PER_BUCKET = 0, 1
 # exported symbols declared in include/shk.h
 EXPORTS = ("shk_build", "shk_build_stats", "shk_query", "shk_serialize", "shk_deserialize",
            "shk_size_bits", "shk_free", "shk_last_error", "shk_leaf_search", "shk_leaf_search_noalloc",
-           "shk_leaf_tune", "shk_leaf_configs", "shk_leaf_graph_replays", "shk_version")
+           "shk_leaf_tune", "shk_leaf_configs", "shk_leaf_graph_replays", "shk_server_create",
+           "shk_server_submit", "shk_server_poll", "shk_server_wait", "shk_server_get_stats",
+           "shk_server_destroy", "shk_version")
 
 
 class ShkError(RuntimeError):
@@ -57,6 +59,17 @@ class _Stats(ctypes.Structure):
                 + [("leaf_launches", ctypes.c_uint64), ("leaf_cfg", ctypes.c_uint32 * 4)])
 
 
+class _ReqInfo(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32), ("n_keys", ctypes.c_uint64),
+                ("footprint_bytes", ctypes.c_uint64), ("submit_ns", ctypes.c_uint64),
+                ("start_ns", ctypes.c_uint64), ("finish_ns", ctypes.c_uint64)]
+
+
+class _SrvStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "queued", "running", "budget_bytes",
+                                               "in_use_bytes", "peak_in_use_bytes")] + [("workers", ctypes.c_uint32)]
+
+
 _lib = None
 
 
@@ -83,6 +96,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "shk_leaf_tune": (i32, [u32, vp, vp, i32, vp]),
         "shk_leaf_configs": (u32, [vp, u32]),
         "shk_leaf_graph_replays": (u64, []),
+        "shk_server_create": (i32, [u64, u32, ctypes.POINTER(vp)]),
+        "shk_server_submit": (i32, [vp, ctypes.POINTER(_Keys), ctypes.POINTER(_Opts), ctypes.POINTER(u64)]),
+        "shk_server_poll": (i32, [vp, u64, ctypes.POINTER(vp), ctypes.POINTER(_ReqInfo)]),
+        "shk_server_wait": (i32, [vp, u64, ctypes.POINTER(vp), ctypes.POINTER(_ReqInfo)]),
+        "shk_server_get_stats": (i32, [vp, ctypes.POINTER(_SrvStats)]),
+        "shk_server_destroy": (None, [vp]),
         "shk_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -324,3 +343,51 @@ def shk_leaf_tune(leaf_size: int, probe_all: bool = False) -> dict:
 
 def shk_leaf_graph_replays() -> int:
     return int(load_library().shk_leaf_graph_replays())
+
+
+# --- serving -------------------------------------------------------------------
+def shk_server_create(hbm_budget_bytes: int = 0, workers: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(load_library().shk_server_create(hbm_budget_bytes, workers, ctypes.byref(out)))
+    return out.value
+
+
+def shk_server_submit(server: int, keys, leaf_size: int, bucket_size: int, *, kind: int = SHK_KEYS_U64,
+                      str_offsets=None, **opt) -> int:
+    k, keep = _as_keys(keys, kind, str_offsets)
+    o = _Opts(leaf_size, bucket_size, opt.get("shard_buckets", 0), opt.get("eps_num", 0), opt.get("sched", 0),
+              opt.get("seeds_per_lane", 0), opt.get("chunk_passes", 0), 0, opt.get("warps_per_block", 0),
+              opt.get("key_unroll", 0))
+    rid = ctypes.c_uint64()
+    _check(load_library().shk_server_submit(server, ctypes.byref(k), ctypes.byref(o), ctypes.byref(rid)))
+    del keep
+    return rid.value
+
+
+def _info_dict(info):
+    return {name: getattr(info, name) for name, _ in _ReqInfo._fields_}
+
+
+def shk_server_poll(server: int, req_id: int):
+    """(Mphf or None, info dict); None while pending (info['done'] == 0)."""
+    out = ctypes.c_void_p()
+    info = _ReqInfo()
+    _check(load_library().shk_server_poll(server, req_id, ctypes.byref(out), ctypes.byref(info)))
+    return (Mphf(out.value) if out.value else None), _info_dict(info)
+
+
+def shk_server_wait(server: int, req_id: int):
+    out = ctypes.c_void_p()
+    info = _ReqInfo()
+    _check(load_library().shk_server_wait(server, req_id, ctypes.byref(out), ctypes.byref(info)))
+    return (Mphf(out.value) if out.value else None), _info_dict(info)
+
+
+def shk_server_get_stats(server: int) -> dict:
+    s = _SrvStats()
+    _check(load_library().shk_server_get_stats(server, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in _SrvStats._fields_}
+
+
+def shk_server_destroy(server: int) -> None:
+    load_library().shk_server_destroy(server)

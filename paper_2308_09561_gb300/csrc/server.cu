@@ -1,0 +1,250 @@
+// server.cu -- serving: a request loop over MPHF builds of different sizes.
+//
+// Requests are queued first in, first out.  A pool of worker threads, each
+// with its own CUDA stream, admits the request at the head of the queue as
+// soon as a worker is free and the request's estimated device footprint fits
+// in what the budget leaves; a request larger than the whole budget runs alone.
+// Builds of different requests run concurrently on their streams, so their
+// kernels overlap on the GPU, and new requests are admitted while others run.
+// Each build is exactly shk_build on the request's keys and options.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace {
+
+uint64_t now_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Request {
+  uint64_t id = 0;
+  int32_t kind = 0;
+  std::vector<uint8_t> data;      // host copy of the keys
+  std::vector<uint64_t> offsets;  // string keys
+  uint64_t n_keys = 0;
+  shk_build_opts opts{};
+  shk_request_info info{};
+  shk_mphf* result = nullptr;
+};
+
+// Device bytes a build holds while it runs: keys staged on the device, three
+// fingerprint copies, bucket ids, orientation bits, per-leaf and per-bucket
+// arrays, the encoded result; plus a fixed allowance.
+uint64_t footprint(uint64_t n_keys, const shk_build_opts& o, uint64_t key_bytes) {
+  const uint64_t b = o.bucket_size ? o.bucket_size : 1;
+  const uint64_t buckets = n_keys / b + 1;
+  return key_bytes + n_keys * 64 + buckets * 96 + (8ull << 20);
+}
+
+}  // namespace
+
+struct shk_server {
+  int device = 0;
+  uint64_t budget = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;
+  std::unordered_map<uint64_t, Request*> all;
+  std::vector<std::thread> threads;
+  uint64_t next_id = 1, in_use = 0, peak = 0, submitted = 0, completed = 0, running = 0;
+  bool stop = false;
+
+  void worker() {
+    cudaSetDevice(device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    for (;;) {
+      Request* r = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_work.wait(lk, [&] {
+          if (stop) return true;
+          if (queue.empty()) return false;
+          const uint64_t fp = queue.front()->info.footprint_bytes;
+          return in_use + fp <= budget || running == 0;
+        });
+        if (stop) break;
+        r = queue.front();
+        queue.pop_front();
+        in_use += r->info.footprint_bytes;
+        if (in_use > peak) peak = in_use;
+        running++;
+        r->info.start_ns = now_ns();
+      }
+      shk_keys k;
+      k.kind = r->kind;
+      k.on_device = 0;
+      k.data = r->data.data();
+      k.str_offsets = r->offsets.empty() ? nullptr : r->offsets.data();
+      k.n_keys = r->n_keys;
+      shk_mphf* m = nullptr;
+      const shk_status s = shk_build(&k, &r->opts, st, &m);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        r->result = m;
+        r->info.status = s;
+        r->info.done = 1;
+        r->info.finish_ns = now_ns();
+        r->data.clear();
+        r->data.shrink_to_fit();
+        r->offsets.clear();
+        r->offsets.shrink_to_fit();
+        in_use -= r->info.footprint_bytes;
+        running--;
+        completed++;
+      }
+      cv_done.notify_all();
+      cv_work.notify_all();
+    }
+    if (st) cudaStreamDestroy(st);
+  }
+};
+
+using namespace shk;
+
+extern "C" shk_status shk_server_create(uint64_t hbm_budget_bytes, uint32_t workers,
+                                        shk_server** out) {
+  if (!out) return fail(SHK_EINVAL, "NULL argument");
+  *out = nullptr;
+  shk_server* s = new shk_server();
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    return fail(SHK_ECUDA, "cudaGetDevice failed");
+  }
+  if (hbm_budget_bytes == 0) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      delete s;
+      return fail(SHK_ECUDA, "cudaMemGetInfo failed");
+    }
+    hbm_budget_bytes = (uint64_t)(free_b * 0.8);
+  }
+  s->budget = hbm_budget_bytes;
+  const uint32_t w = workers ? workers : 4;
+  for (uint32_t i = 0; i < w; i++) s->threads.emplace_back([s] { s->worker(); });
+  *out = s;
+  return SHK_OK;
+}
+
+extern "C" shk_status shk_server_submit(shk_server* srv, const shk_keys* keys,
+                                        const shk_build_opts* opts, uint64_t* req_id) {
+  if (!srv || !keys || !opts || !req_id) return fail(SHK_EINVAL, "NULL argument");
+  if (keys->kind != SHK_KEYS_U64 && keys->kind != SHK_KEYS_STR && keys->kind != SHK_KEYS_FP128)
+    return fail(SHK_EINVAL, "unknown key kind");
+  const uint64_t N = keys->n_keys;
+  if (N && !keys->data) return fail(SHK_EINVAL, "key data is NULL");
+  if (keys->kind == SHK_KEYS_STR && N && !keys->str_offsets)
+    return fail(SHK_EINVAL, "string keys need str_offsets");
+  Request* r = new Request();
+  r->kind = keys->kind;
+  r->n_keys = N;
+  r->opts = *opts;
+  r->opts.profile = 0;
+  // copy the keys now: the caller's buffers are only borrowed for this call
+  const cudaMemcpyKind dir = keys->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  if (keys->kind == SHK_KEYS_STR) {
+    r->offsets.resize(N + 1);
+    if (cudaMemcpy(r->offsets.data(), keys->str_offsets, (N + 1) * 8, dir) != cudaSuccess) {
+      delete r;
+      return fail(SHK_ECUDA, "copying string offsets failed");
+    }
+    const uint64_t base = r->offsets[0], total = r->offsets[N] - base;
+    r->data.resize(total + 8);
+    if (total && cudaMemcpy(r->data.data(), (const uint8_t*)keys->data + base, total, dir) != cudaSuccess) {
+      delete r;
+      return fail(SHK_ECUDA, "copying string keys failed");
+    }
+    for (auto& v : r->offsets) v -= base;
+  } else {
+    const uint64_t bytes = N * (keys->kind == SHK_KEYS_U64 ? 8 : 16);
+    r->data.resize(bytes ? bytes : 8);
+    if (bytes && cudaMemcpy(r->data.data(), keys->data, bytes, dir) != cudaSuccess) {
+      delete r;
+      return fail(SHK_ECUDA, "copying keys failed");
+    }
+  }
+  r->info.n_keys = N;
+  r->info.footprint_bytes = footprint(N, *opts, r->data.size());
+  r->info.submit_ns = now_ns();
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    r->id = srv->next_id++;
+    srv->all[r->id] = r;
+    srv->queue.push_back(r);
+    srv->submitted++;
+  }
+  srv->cv_work.notify_all();
+  *req_id = r->id;
+  return SHK_OK;
+}
+
+static shk_status poll_locked(shk_server* srv, uint64_t req_id, shk_mphf** out,
+                              shk_request_info* info, std::unique_lock<std::mutex>& lk, bool wait) {
+  auto it = srv->all.find(req_id);
+  if (it == srv->all.end()) return fail(SHK_EINVAL, "unknown request id");
+  Request* r = it->second;
+  if (wait) srv->cv_done.wait(lk, [&] { return r->info.done != 0; });
+  if (info) *info = r->info;
+  if (out) *out = nullptr;
+  if (!r->info.done) return SHK_OK;
+  if (out)
+    *out = r->result;
+  else if (r->result)
+    shk_free(r->result);
+  srv->all.erase(it);
+  delete r;
+  return SHK_OK;
+}
+
+extern "C" shk_status shk_server_poll(shk_server* srv, uint64_t req_id, shk_mphf** out,
+                                      shk_request_info* info) {
+  if (!srv) return fail(SHK_EINVAL, "NULL argument");
+  std::unique_lock<std::mutex> lk(srv->mu);
+  return poll_locked(srv, req_id, out, info, lk, false);
+}
+
+extern "C" shk_status shk_server_wait(shk_server* srv, uint64_t req_id, shk_mphf** out,
+                                      shk_request_info* info) {
+  if (!srv) return fail(SHK_EINVAL, "NULL argument");
+  std::unique_lock<std::mutex> lk(srv->mu);
+  return poll_locked(srv, req_id, out, info, lk, true);
+}
+
+extern "C" shk_status shk_server_get_stats(shk_server* srv, shk_server_stats* out) {
+  if (!srv || !out) return fail(SHK_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  out->submitted = srv->submitted;
+  out->completed = srv->completed;
+  out->queued = srv->queue.size();
+  out->running = srv->running;
+  out->budget_bytes = srv->budget;
+  out->in_use_bytes = srv->in_use;
+  out->peak_in_use_bytes = srv->peak;
+  out->workers = (uint32_t)srv->threads.size();
+  return SHK_OK;
+}
+
+extern "C" void shk_server_destroy(shk_server* srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv_work.notify_all();
+  for (auto& t : srv->threads) t.join();
+  for (auto& kv : srv->all) {
+    if (kv.second->result) shk_free(kv.second->result);
+    delete kv.second;
+  }
+  delete srv;
+}
