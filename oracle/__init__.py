@@ -76,12 +76,16 @@ def _load():
             "orc_leaf_seed": (i32, [vp, u32, u64, u64, i32, vp]),
             "orc_leaf_seed_stats": (None, [vp, u32, u64, u64, vp, vp]),
             "orc_orient": (i32, [vp, u32, u64, vp]),
-            "orc_leaf_search_batch": (i32, [vp, vp, u32, u64, vp, vp, i32]),
-            "orc_bucket_build": (i32, [vp, vp, u32, u32, vp, vp, u32, vp, vp]),
+            "orc_leaf_search_batch": (i32, [vp, vp, u32, u64, vp, vp, i32, i32]),
+            "orc_bucket_build": (i32, [vp, vp, u32, u32, vp, vp, u32, vp, vp, i32]),
+            "orc_rf_set": (i32, [u64]),
+            "orc_rf_cells": (None, [u64, u64, u32, vp, vp]),
+            "orc_rf_value": (i32, [vp, u32, u64, u64, i32, vp]),
+            "orc_orient_mode": (i32, [i32, vp, u32, u64, vp]),
             "orc_ribbon_shard": (i32, [vp, vp, vp, u64, u32, vp, vp]),
             "orc_shard_slots": (u64, [u64, u32]),
             "orc_default_shard_buckets": (u32, [u32]),
-            "orc_build": (i32, [i32, vp, vp, u64, u32, u32, u32, u32, i32, vp, vp]),
+            "orc_build": (i32, [i32, vp, vp, u64, u32, u32, u32, u32, i32, i32, vp, vp]),
             "orc_query": (i32, [vp, u64, vp, vp, u64, vp]),
             "orc_free": (None, [vp]),
         }
@@ -214,20 +218,51 @@ def orient(x, seed: int) -> np.ndarray:
     return f
 
 
-def leaf_search_batch(x, leaf_off, seed_start: int = 0, nthreads: int = 0):
-    """First passing seed >= seed_start per leaf, and f as a bit mask per leaf."""
+def leaf_search_batch(x, leaf_off, seed_start: int = 0, nthreads: int = 0, rf: bool = False):
+    """First passing seed (or rotation-fitting value) >= seed_start per leaf,
+    and f as a bit mask per leaf."""
     x = _u64(x)
     off = np.ascontiguousarray(leaf_off, dtype=np.uint32)
     nl = off.size - 1
     seeds = np.zeros(nl, np.uint64)
     fm = np.zeros(nl, np.uint64)
-    st = _load().orc_leaf_search_batch(_p(x), _p(off), nl, seed_start, _p(seeds), _p(fm), nthreads)
+    st = _load().orc_leaf_search_batch(_p(x), _p(off), nl, seed_start, _p(seeds), _p(fm), nthreads,
+                                       int(rf))
     if st:
         raise OracleError(st, "leaf_search_batch")
     return seeds, fm
 
 
-def bucket_build(lo_sorted, hi_sorted, n: int):
+def rf_set(x: int) -> int:
+    return int(_load().orc_rf_set(x))
+
+
+def rf_cells(x: int, v: int, m: int) -> tuple[int, int]:
+    h0 = ctypes.c_uint32()
+    h1 = ctypes.c_uint32()
+    _load().orc_rf_cells(x, v, m, ctypes.byref(h0), ctypes.byref(h1))
+    return h0.value, h1.value
+
+
+def rf_value(x, start: int = 0, cap: int = SEED_CAP, use_filter: bool = True) -> int:
+    x = _u64(x)
+    v = ctypes.c_uint64()
+    st = _load().orc_rf_value(_p(x), x.size, start, cap, int(use_filter), ctypes.byref(v))
+    if st:
+        raise OracleError(st, "rf_value")
+    return v.value
+
+
+def orient_mode(x, value: int, rf: bool) -> np.ndarray:
+    x = _u64(x)
+    f = np.zeros(x.size, np.uint8)
+    st = _load().orc_orient_mode(int(rf), _p(x), x.size, value, _p(f))
+    if st:
+        raise OracleError(st, "orient_mode")
+    return f
+
+
+def bucket_build(lo_sorted, hi_sorted, n: int, rf: bool = False):
     """One bucket: (codes [(seed, k)] in preorder, lo, hi in leaf order, f)."""
     lo = _u64(lo_sorted).copy()
     hi = _u64(hi_sorted).copy()
@@ -237,7 +272,8 @@ def bucket_build(lo_sorted, hi_sorted, n: int):
     ks = np.zeros(cap, np.uint8)
     nc = ctypes.c_uint32()
     f = np.zeros(max(size, 1), np.uint8)
-    st = _load().orc_bucket_build(_p(lo), _p(hi), size, n, _p(seeds), _p(ks), cap, ctypes.byref(nc), _p(f))
+    st = _load().orc_bucket_build(_p(lo), _p(hi), size, n, _p(seeds), _p(ks), cap, ctypes.byref(nc), _p(f),
+                                  int(rf))
     if st:
         raise OracleError(st, "bucket_build")
     return seeds[: nc.value].copy(), ks[: nc.value].copy(), lo, hi, f[:size].copy()
@@ -267,8 +303,9 @@ def ribbon_shard(lo, hi, f, eps_num: int = DEFAULT_EPS_NUM):
 
 def build_mphf(keys=None, *, kind: int = KEYS_U64, str_data=None, str_offsets=None, fp=None,
                n: int = 32, b: int = 2000, shard_buckets: int | None = None,
-               eps_num: int = DEFAULT_EPS_NUM, nthreads: int = 0) -> bytes:
-    """Whole construction -> serialized MPHF bytes."""
+               eps_num: int = DEFAULT_EPS_NUM, nthreads: int = 0, leaf_mode: int = 0) -> bytes:
+    """Whole construction -> serialized MPHF bytes.  leaf_mode 0: plain
+    ShockHash leaves; 1: rotation fitting with partial hash calculation."""
     lib = _load()
     if shard_buckets is None:
         shard_buckets = default_shard_buckets(b)
@@ -288,7 +325,7 @@ def build_mphf(keys=None, *, kind: int = KEYS_U64, str_data=None, str_offsets=No
     out = ctypes.c_void_p()
     ln = ctypes.c_uint64()
     st = lib.orc_build(kind, _p(data), _p(offs) if offs is not None else None, N, n, b,
-                       shard_buckets, eps_num, nthreads, ctypes.byref(out), ctypes.byref(ln))
+                       shard_buckets, eps_num, nthreads, leaf_mode, ctypes.byref(out), ctypes.byref(ln))
     if st:
         raise OracleError(st, "build")
     try:

@@ -68,6 +68,8 @@ enum { ORC_KEYS_U64 = 0, ORC_KEYS_STR = 1, ORC_KEYS_FP128 = 2 };
 #define RET_SALT2 0x3F84D5B5B5470917ull
 #define STR_SALT_A 0x9216D5D98979FB1Bull
 #define STR_SALT_B 0xD1310BA698DFB5ACull
+#define RF_SALT 0x2FFD72DBD01ADFB7ull
+#define RF_PARTIAL_K 8u  /* App. A.2: the first set keeps seed x - (x mod k), k = 8 */
 
 /* Rice parameter of a leaf of m keys: floor(log2(ln2 * mu(m))) with mu(m) the
  * mean number of seeds tried, mu ~ 0.8 (e/2)^m e / sqrt(pi m) (the paper's
@@ -297,6 +299,45 @@ int orc_leaf_seed(const uint64_t* x, uint32_t m, uint64_t start, uint64_t cap, i
   return ORC_ESEEDCAP;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Rotation fitting (Sec. 4, Rotation Fitting) with partial hash calculation */
+/* (App. A.2).  Reading: a fixed 1-bit hash puts key x in set B when        */
+/* mix(x ^ RF_SALT) has its top bit set, else in set A.  Candidate v = s*m+r */
+/* (seed s, rotation r in [0, m)): keys of A take the cells of seed s_A,     */
+/* keys of B the cells of seed s moved by r (mod m) -- the cyclic rotation  */
+/* of B's bit mask.  s_A = s - (s mod 8) for leaves of more than 32 keys    */
+/* (the first set is hashed with a seed fixed over 8 consecutive seeds),    */
+/* s_A = s otherwise.  The leaf value is the smallest pseudoforest v.       */
+/* ------------------------------------------------------------------------ */
+int orc_rf_set(uint64_t x) { return (int)(orc_mix64(x ^ RF_SALT) >> 63); }
+
+void orc_rf_cells(uint64_t x, uint64_t v, uint32_t m, uint32_t* h0, uint32_t* h1) {
+  uint64_t s = v / m, r = v % m;
+  if (!orc_rf_set(x)) {
+    uint64_t sa = m > 32 ? s - s % RF_PARTIAL_K : s;
+    orc_leaf_hash(x, sa, m, h0, h1);
+  } else {
+    orc_leaf_hash(x, s, m, h0, h1);
+    *h0 = (uint32_t)((*h0 + r) % m);
+    *h1 = (uint32_t)((*h1 + r) % m);
+  }
+}
+
+int orc_rf_value(const uint64_t* x, uint32_t m, uint64_t start, uint64_t cap, int use_filter,
+                 uint64_t* v_out) {
+  uint32_t h0[ORC_MAX_LEAF], h1[ORC_MAX_LEAF];
+  if (m < 2 || m > ORC_MAX_LEAF) return ORC_EINVAL;
+  for (uint64_t v = start; v < cap; v++) {
+    for (uint32_t i = 0; i < m; i++) orc_rf_cells(x[i], v, m, &h0[i], &h1[i]);
+    if (use_filter && !orc_covers_all(h0, h1, m)) continue;
+    if (orc_is_pseudoforest(h0, h1, m)) {
+      *v_out = v;
+      return ORC_OK;
+    }
+  }
+  return ORC_ESEEDCAP;
+}
+
 /* Over seeds s0 .. s0+count-1 of one leaf: how many pass the filter and how
  * many give a pseudoforest (for the filter-rate and trial-count pins). */
 void orc_leaf_seed_stats(const uint64_t* x, uint32_t m, uint64_t s0, uint64_t count,
@@ -361,18 +402,9 @@ static int bijection_exists(uint32_t m, const uint32_t* h0, const uint32_t* h1, 
   return 1;
 }
 
-int orc_orient(const uint64_t* x, uint32_t m, uint64_t seed, uint8_t* f) {
-  uint32_t h0[ORC_MAX_LEAF], h1[ORC_MAX_LEAF];
+static int orient_cells(const uint32_t* h0, const uint32_t* h1, uint32_t m, uint8_t* f) {
   int fixed[ORC_MAX_LEAF];
-  if (m == 1) {
-    f[0] = 0;
-    return ORC_OK;
-  }
-  if (m < 2 || m > ORC_MAX_LEAF) return ORC_EINVAL;
-  for (uint32_t i = 0; i < m; i++) {
-    orc_leaf_hash(x[i], seed, m, &h0[i], &h1[i]);
-    fixed[i] = -1;
-  }
+  for (uint32_t i = 0; i < m; i++) fixed[i] = -1;
   if (!bijection_exists(m, h0, h1, fixed)) return ORC_EINVAL;
   for (uint32_t i = 0; i < m; i++) {
     fixed[i] = 0;
@@ -382,11 +414,36 @@ int orc_orient(const uint64_t* x, uint32_t m, uint64_t seed, uint8_t* f) {
   return ORC_OK;
 }
 
+/* The leaf's cells under its stored value: a seed (plain) or v (rotation
+ * fitting). */
+static void leaf_cells_mode(int rf, uint64_t x, uint64_t value, uint32_t m, uint32_t* h0,
+                            uint32_t* h1) {
+  if (rf)
+    orc_rf_cells(x, value, m, h0, h1);
+  else
+    orc_leaf_hash(x, value, m, h0, h1);
+}
+
+int orc_orient_mode(int rf, const uint64_t* x, uint32_t m, uint64_t value, uint8_t* f) {
+  uint32_t h0[ORC_MAX_LEAF], h1[ORC_MAX_LEAF];
+  if (m == 1) {
+    f[0] = 0;
+    return ORC_OK;
+  }
+  if (m < 2 || m > ORC_MAX_LEAF) return ORC_EINVAL;
+  for (uint32_t i = 0; i < m; i++) leaf_cells_mode(rf, x[i], value, m, &h0[i], &h1[i]);
+  return orient_cells(h0, h1, m, f);
+}
+
+int orc_orient(const uint64_t* x, uint32_t m, uint64_t seed, uint8_t* f) {
+  return orc_orient_mode(0, x, m, seed, f);
+}
+
 /* Batched leaf search over independent leaves (same definitions as above):
  * leaf i holds x[leaf_off[i] .. leaf_off[i+1]).  f_mask bit j = f of key j. */
 int orc_leaf_search_batch(const uint64_t* x, const uint32_t* leaf_off, uint32_t n_leaves,
                           uint64_t seed_start, uint64_t* seeds_out, uint64_t* f_mask,
-                          int nthreads) {
+                          int nthreads, int rf) {
   int status = ORC_OK;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -403,8 +460,11 @@ int orc_leaf_search_batch(const uint64_t* x, const uint32_t* leaf_off, uint32_t 
       s = seed_start;
       f[0] = 0;
     } else {
-      st = orc_leaf_seed(x + leaf_off[i], m, seed_start, ORC_SEED_CAP, 1, &s);
-      if (st == ORC_OK) st = orc_orient(x + leaf_off[i], m, s, f);
+      if (rf)
+        st = orc_rf_value(x + leaf_off[i], m, seed_start, ORC_SEED_CAP, 1, &s);
+      else
+        st = orc_leaf_seed(x + leaf_off[i], m, seed_start, ORC_SEED_CAP, 1, &s);
+      if (st == ORC_OK) st = orc_orient_mode(rf, x + leaf_off[i], m, s, f);
     }
     if (st != ORC_OK) {
 #pragma omp critical
@@ -515,7 +575,7 @@ static int codes_push(codes_t* c, uint64_t seed, uint32_t k) {
 }
 
 static int build_node(uint64_t* lo, uint64_t* hi, uint8_t* f, uint32_t m, uint32_t n,
-                      codes_t* codes, uint64_t* tlo, uint64_t* thi) {
+                      codes_t* codes, uint64_t* tlo, uint64_t* thi, int rf) {
   uint32_t unit, fan;
   if (!orc_split_shape(m, n, &unit, &fan)) {
     if (m == 1) {
@@ -523,10 +583,11 @@ static int build_node(uint64_t* lo, uint64_t* hi, uint8_t* f, uint32_t m, uint32
       return ORC_OK;
     }
     uint64_t s;
-    int st = orc_leaf_seed(lo, m, 0, ORC_SEED_CAP, 1, &s);
+    int st = rf ? orc_rf_value(lo, m, 0, ORC_SEED_CAP, 1, &s)
+                : orc_leaf_seed(lo, m, 0, ORC_SEED_CAP, 1, &s);
     if (st != ORC_OK) return st;
     if (!codes_push(codes, s, orc_rice_k_leaf(m))) return ORC_ENOMEM;
-    return orc_orient(lo, m, s, f);
+    return orc_orient_mode(rf, lo, m, s, f);
   }
   uint64_t s;
   int st = orc_split_seed(lo, m, n, &s);
@@ -546,7 +607,7 @@ static int build_node(uint64_t* lo, uint64_t* hi, uint8_t* f, uint32_t m, uint32
   uint32_t off = 0;
   for (uint32_t j = 0; j < fan; j++) {
     uint32_t p = part_size(m, unit, fan, j);
-    st = build_node(lo + off, hi + off, f + off, p, n, codes, tlo, thi);
+    st = build_node(lo + off, hi + off, f + off, p, n, codes, tlo, thi, rf);
     if (st != ORC_OK) return st;
     off += p;
   }
@@ -556,7 +617,7 @@ static int build_node(uint64_t* lo, uint64_t* hi, uint8_t* f, uint32_t m, uint32
 /* Bucket-level entry point for sampled parity: keys sorted ascending on
  * input, reordered into leaf order on output; codes in preorder. */
 int orc_bucket_build(uint64_t* lo, uint64_t* hi, uint32_t size, uint32_t n, uint64_t* seeds,
-                     uint8_t* ks, uint32_t cap, uint32_t* ncodes, uint8_t* f) {
+                     uint8_t* ks, uint32_t cap, uint32_t* ncodes, uint8_t* f, int rf) {
   if (size == 0) {
     *ncodes = 0;
     return ORC_OK;
@@ -564,7 +625,7 @@ int orc_bucket_build(uint64_t* lo, uint64_t* hi, uint32_t size, uint32_t n, uint
   codes_t c = {0};
   uint64_t* tlo = (uint64_t*)malloc((size_t)size * 8);
   uint64_t* thi = (uint64_t*)malloc((size_t)size * 8);
-  int st = (tlo && thi) ? build_node(lo, hi, f, size, n, &c, tlo, thi) : ORC_ENOMEM;
+  int st = (tlo && thi) ? build_node(lo, hi, f, size, n, &c, tlo, thi, rf) : ORC_ENOMEM;
   if (st == ORC_OK) {
     if (c.n > cap) st = ORC_EINVAL;
     else {
@@ -737,12 +798,12 @@ uint32_t orc_default_shard_buckets(uint32_t b) {
 }
 
 int orc_build(int kind, const void* data, const uint64_t* offs, uint64_t N, uint32_t n,
-              uint32_t b, uint32_t shard_buckets, uint32_t eps_num, int nthreads, uint8_t** out,
-              uint64_t* out_len) {
+              uint32_t b, uint32_t shard_buckets, uint32_t eps_num, int nthreads, int leaf_mode,
+              uint8_t** out, uint64_t* out_len) {
   *out = NULL;
   *out_len = 0;
   if (n < 2 || n > ORC_MAX_LEAF || b < n || b > ORC_MAX_BUCKET_SIZE || shard_buckets == 0 ||
-      N >= (1ull << 32))
+      N >= (1ull << 32) || (leaf_mode != 0 && leaf_mode != 1))
     return ORC_EINVAL;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -810,8 +871,9 @@ int orc_build(int kind, const void* data, const uint64_t* offs, uint64_t N, uint
     if (size == 0) continue;
     uint64_t* tlo = (uint64_t*)malloc((size_t)size * 8);
     uint64_t* thi = (uint64_t*)malloc((size_t)size * 8);
-    int st = (tlo && thi) ? build_node(lo + K[i], hi + K[i], f + K[i], size, n, &bc[i], tlo, thi)
-                          : ORC_ENOMEM;
+    int st = (tlo && thi)
+                 ? build_node(lo + K[i], hi + K[i], f + K[i], size, n, &bc[i], tlo, thi, leaf_mode)
+                 : ORC_ENOMEM;
     free(tlo);
     free(thi);
     if (st != ORC_OK) {
@@ -870,7 +932,8 @@ int orc_build(int kind, const void* data, const uint64_t* offs, uint64_t N, uint
       goto done;
     }
     uint64_t hdr[ORC_HEADER_WORDS] = {ORC_MAGIC, N, n, b, B, shard_buckets, eps_num, num_shards,
-                                      rice.nbits, lK, kh.nbits, lO, oh.nbits, rib_bits, 0, 0};
+                                      rice.nbits, lK, kh.nbits, lO, oh.nbits, rib_bits,
+                                      (uint64_t)leaf_mode, 0};
     uint64_t pw = 0;
     put_words(blob, &pw, hdr, ORC_HEADER_WORDS);
     put_words(blob, &pw, rice.w, w_rice);
@@ -919,7 +982,7 @@ done:
 /* h_{s,f(x)}(x)).  Decodes the tree from the bucket's Rice stream.          */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  uint64_t N, n, b, B, shard_buckets, eps_num, num_shards;
+  uint64_t N, n, b, B, shard_buckets, eps_num, num_shards, leaf_mode;
   const uint64_t* rice;
   const uint8_t* seeds;
   const uint64_t* rib;
@@ -959,7 +1022,7 @@ static uint64_t query_one(const mphf_view_t* v, uint64_t lo, uint64_t hi) {
   if (m >= 2) {
     uint64_t s = rice_get(v->rice, &pos, orc_rice_k_leaf(m));
     uint32_t h0, h1;
-    orc_leaf_hash(lo, s, m, &h0, &h1);
+    leaf_cells_mode((int)v->leaf_mode, lo, s, m, &h0, &h1);
     uint64_t sh = bkt / v->shard_buckets;
     uint64_t b0 = sh * v->shard_buckets;
     uint64_t b1 = b0 + v->shard_buckets < v->B ? b0 + v->shard_buckets : v->B;
@@ -987,6 +1050,8 @@ int orc_query(const uint8_t* blob, uint64_t len, const uint64_t* lo, const uint6
   v.shard_buckets = h[5];
   v.eps_num = h[6];
   v.num_shards = h[7];
+  v.leaf_mode = h[14];
+  if (v.leaf_mode > 1) return ORC_EFORMAT;
   uint64_t rice_bits = h[8], lK = h[9], khb = h[10], lO = h[11], ohb = h[12], rib = h[13];
   if (v.N == 0) return nq == 0 ? ORC_OK : ORC_EINVAL;
   uint64_t pw = ORC_HEADER_WORDS;

@@ -11,7 +11,7 @@ import numpy as np
 
 HEADER = ["magic", "N", "n", "b", "B", "shard_buckets", "eps_num", "num_shards",
           "rice_bits", "efK_l", "efK_hi_bits", "efO_l", "efO_hi_bits", "ribbon_bits",
-          "reserved0", "reserved1"]
+          "leaf_mode", "reserved"]
 
 
 def _words(nbits):
