@@ -252,6 +252,19 @@ def run_ours(args):
         st = m.stats()
         t_cmp[name] = st
         m.close()
+    # rotation fitting with partial hash calculation (leaf mode 1) on the same keys
+    rf_stats = []
+    for _ in range(3):
+        m = pkg.shk_build(dkeys, LEAF, BUCKET, leaf_mode=pkg.SHK_LEAF_ROTATION, profile=True)
+        rf_stats.append(m.stats())
+        rf_bytes = len(m.serialize())
+        m.close()
+    rf_ms = float(np.median([s["ms_total"] for s in rf_stats]))
+    rotation = {"keys_per_s": N_KEYS / (rf_ms / 1e3), "ms_total": rf_ms,
+                "ms_leaf": float(np.median([s["ms_leaf"] for s in rf_stats])),
+                "leaf_candidates_per_s": rf_stats[-1]["leaf_seeds_min"] / (rf_stats[-1]["ms_leaf"] / 1e3),
+                "bits_per_key": 8 * rf_bytes / N_KEYS,
+                "note": "candidates = sum over leaves of (v+1), v = seed*m + rotation"}
     per_bucket = {"keys": cmp_keys, "persistent_ms_leaf": t_cmp["persistent"]["ms_leaf"],
                   "per_bucket_ms_leaf": t_cmp["per_bucket"]["ms_leaf"],
                   "per_bucket_leaf_launches": t_cmp["per_bucket"]["leaf_launches"],
@@ -282,6 +295,7 @@ def run_ours(args):
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "leaf_kernel_cfg": stats[-1]["leaf_cfg"],
         "persistent_vs_per_bucket": per_bucket,
+        "rotation_fitting": rotation,
         "wall_s_timed": wall,
     }
     if clocks:

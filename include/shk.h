@@ -71,6 +71,14 @@ typedef enum {
   SHK_SCHED_PER_BUCKET = 1      /* one launch per bucket, one warp per leaf     */
 } shk_sched;
 
+/* How leaves are solved (both are ShockHash: the smallest value whose graph
+ * is a pseudoforest). */
+typedef enum {
+  SHK_LEAF_PLAIN = 0,    /* value = seed s (Sec. 4, Eq. ShockHash)                  */
+  SHK_LEAF_ROTATION = 1  /* value = s*m + r: rotation fitting with partial hash     */
+                         /* calculation (Sec. 4 Rotation Fitting, App. A.2)       */
+} shk_leaf_mode;
+
 /* Build options.  Zero-initialise and set leaf_size and bucket_size; zero in
  * any other field selects its default. */
 typedef struct {
@@ -85,6 +93,7 @@ typedef struct {
   uint32_t profile;          /* 1: time each phase with CUDA events              */
   uint32_t warps_per_block;  /* with seeds_per_lane != 0: 4, 8 or 16; 0 = 8      */
   uint32_t key_unroll;       /* with seeds_per_lane != 0: 1, 2 or 4; 0 = 2       */
+  uint32_t leaf_mode;        /* shk_leaf_mode; recorded in the encoded header     */
 } shk_build_opts;
 
 /* Statistics of the build that produced an MPHF (shk_build_stats). */

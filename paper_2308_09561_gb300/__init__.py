@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libshk_gpu.so")
 SHK_OK, SHK_EINVAL, SHK_EDUPKEY, SHK_ENOMEM, SHK_ECUDA, SHK_ESEEDCAP, SHK_ETIMEOUT, SHK_EFORMAT = range(8)
 SHK_KEYS_U64, SHK_KEYS_STR, SHK_KEYS_FP128 = 0, 1, 2
 SHK_SCHED_PERSISTENT, SHK_SCHED_PER_BUCKET = 0, 1
+SHK_LEAF_PLAIN, SHK_LEAF_ROTATION = 0, 1
 
 # exported symbols declared in include/shk.h
 EXPORTS = ("shk_build", "shk_build_stats", "shk_query", "shk_serialize", "shk_deserialize",
@@ -45,7 +46,7 @@ class _Keys(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in
                 ("leaf_size", "bucket_size", "shard_buckets", "eps_num", "sched", "seeds_per_lane",
-                 "chunk_passes", "profile", "warps_per_block", "key_unroll")]
+                 "chunk_passes", "profile", "warps_per_block", "key_unroll", "leaf_mode")]
 
 
 _STAT_U64 = ["n_keys", "n_buckets", "n_leaves", "n_search_leaves", "n_split_nodes", "leaf_seeds_min",
@@ -206,11 +207,12 @@ class Mphf:
 def shk_build(keys, leaf_size: int, bucket_size: int, *, kind: int = SHK_KEYS_U64, str_offsets=None,
               shard_buckets: int = 0, eps_num: int = 0, sched: int = SHK_SCHED_PERSISTENT,
               seeds_per_lane: int = 0, chunk_passes: int = 0, profile: bool = False,
-              warps_per_block: int = 0, key_unroll: int = 0, stream=None) -> Mphf:
+              warps_per_block: int = 0, key_unroll: int = 0, leaf_mode: int = SHK_LEAF_PLAIN,
+              stream=None) -> Mphf:
     lib = load_library()
     k, keep = _as_keys(keys, kind, str_offsets)
     o = _Opts(leaf_size, bucket_size, shard_buckets, eps_num, sched, seeds_per_lane, chunk_passes,
-              1 if profile else 0, warps_per_block, key_unroll)
+              1 if profile else 0, warps_per_block, key_unroll, leaf_mode)
     out = ctypes.c_void_p()
     _check(lib.shk_build(ctypes.byref(k), ctypes.byref(o), _stream_handle(stream), ctypes.byref(out)))
     del keep
@@ -357,7 +359,7 @@ def shk_server_submit(server: int, keys, leaf_size: int, bucket_size: int, *, ki
     k, keep = _as_keys(keys, kind, str_offsets)
     o = _Opts(leaf_size, bucket_size, opt.get("shard_buckets", 0), opt.get("eps_num", 0), opt.get("sched", 0),
               opt.get("seeds_per_lane", 0), opt.get("chunk_passes", 0), 0, opt.get("warps_per_block", 0),
-              opt.get("key_unroll", 0))
+              opt.get("key_unroll", 0), opt.get("leaf_mode", 0))
     rid = ctypes.c_uint64()
     _check(load_library().shk_server_submit(server, ctypes.byref(k), ctypes.byref(o), ctypes.byref(rid)))
     del keep

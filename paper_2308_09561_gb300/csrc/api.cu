@@ -160,6 +160,8 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   if (b < n || b > kMaxBucketSize) return fail(SHK_EINVAL, "bucket_size must be in [leaf_size, 4096]");
   if (N >= (1ull << 32)) return fail(SHK_EINVAL, "at most 2^32 - 1 keys");
   if (o->sched > SHK_SCHED_PER_BUCKET) return fail(SHK_EINVAL, "unknown schedule");
+  if (o->leaf_mode > SHK_LEAF_ROTATION) return fail(SHK_EINVAL, "unknown leaf mode");
+  const uint32_t rf = o->leaf_mode;
   const uint32_t S = o->shard_buckets ? o->shard_buckets : std::max(1u, 8192u / b);
   const uint32_t eps = o->eps_num ? o->eps_num : kDefaultEpsNum;
   Ctx c(st);
@@ -167,7 +169,9 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   // leaf kernel configuration: the autotuner's choice for this leaf size,
   // unless the caller fixes it
   LeafCfg cfg;
-  if (o->seeds_per_lane) {
+  if (rf) {
+    cfg = {8u, 8u, 2u, o->chunk_passes ? o->chunk_passes : 2u};
+  } else if (o->seeds_per_lane) {
     cfg = {o->seeds_per_lane, o->warps_per_block ? o->warps_per_block : 8u,
            o->key_unroll ? o->key_unroll : 2u, o->chunk_passes ? o->chunk_passes : 8u};
     if (!leaf_cfg_valid(cfg)) return fail(SHK_EINVAL, "unsupported leaf kernel configuration");
@@ -251,12 +255,13 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   LeafSearchArgs a{leaves, h_L, llo, 0, best, err, counters, cfg};
   uint64_t leaf_launches = 0;
   if (o->sched == SHK_SCHED_PERSISTENT) {
-    SHK_TRY(launch_leaf_persistent(c, a));
+    SHK_TRY(rf ? launch_leaf_rf_persistent(c, a) : launch_leaf_persistent(c, a));
     leaf_launches = h_L ? 1 : 0;
   } else {
     for (uint64_t i = 0; i < B; i++) {
       if (h_leaf_base[i + 1] > h_leaf_base[i]) {
-        SHK_TRY(launch_leaf_range(c, a, h_leaf_base[i], h_leaf_base[i + 1]));
+        SHK_TRY(rf ? launch_leaf_rf_range(c, a, h_leaf_base[i], h_leaf_base[i + 1])
+                   : launch_leaf_range(c, a, h_leaf_base[i], h_leaf_base[i + 1]));
         leaf_launches++;
       }
     }
@@ -266,7 +271,7 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   // a6: orientation (also stores leaf seeds into their code slots)
   uint8_t* f;
   SHK_TRY(c.arena.alloc(&f, N, true));
-  SHK_TRY(launch_orient(c, leaves, h_L, llo, best, codes, f, nullptr, err));
+  SHK_TRY(launch_orient(c, leaves, h_L, llo, best, codes, f, nullptr, err, rf));
   SHK_TRY(launch_leaf_sums(c, leaves, h_L, best, counters + 1));
   const int t5 = pt.mark();
 
@@ -301,7 +306,7 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   const uint32_t lK = ef_low_bits(N, B + 1), lO = ef_low_bits(h_rice_bits, B + 1);
   const uint64_t hdr[kHeaderWords] = {kMagic, N, n, b, B, S, eps, num_shards, h_rice_bits, lK,
                                       (N >> lK) + B + 1, lO, (h_rice_bits >> lO) + B + 1,
-                                      h_rib_bits, 0, 0};
+                                      h_rib_bits, rf, 0};
   memcpy(m->hdr, hdr, sizeof hdr);
   layout(m);
   shk_status rs = SHK_OK;
@@ -424,7 +429,8 @@ extern "C" shk_status shk_deserialize(const uint8_t* buf, size_t len, shk_mphf**
             N < (1ull << 32) && B == (N ? (N + b - 1) / b : 0) && S >= 1 &&
             h[7] == (B + S - 1) / S && h[9] < 64 && h[11] < 64 && h[9] == ef_low_bits(N, B + 1) &&
             h[10] == (N >> h[9]) + B + 1 && h[11] == ef_low_bits(h[8], B + 1) &&
-            h[12] == (h[8] >> h[11]) + B + 1 && h[8] < (1ull << 48) && h[13] < (1ull << 48);
+            h[12] == (h[8] >> h[11]) + B + 1 && h[8] < (1ull << 48) && h[13] < (1ull << 48) &&
+            h[14] <= 1 && h[15] == 0;
   if (ok) {
     layout(m);
     ok = m->words * 8 == len;

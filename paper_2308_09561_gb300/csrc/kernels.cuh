@@ -75,7 +75,10 @@ LeafCfg leaf_cfg_at(int i);
 // and optionally f as a mask per leaf.
 shk_status launch_orient(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves, const uint64_t* x,
                          const unsigned long long* best, uint64_t* codes, uint8_t* f_key,
-                         uint64_t* f_mask, uint32_t* err);
+                         uint64_t* f_mask, uint32_t* err, uint32_t leaf_mode = 0);
+// rotation fitting (leaf mode 1): best[] receives v = s*m + r
+shk_status launch_leaf_rf_persistent(Ctx& c, const LeafSearchArgs& a);
+shk_status launch_leaf_rf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1);
 shk_status launch_leaf_sums(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves,
                             const unsigned long long* best, unsigned long long* sums);
 

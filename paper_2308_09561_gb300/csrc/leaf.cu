@@ -509,7 +509,8 @@ shk_status tuned_leaf_cfg(Ctx& c, uint32_t m, LeafCfg* out) {
 // ---------------------------------------------------------------------------
 __global__ void k_orient(const LeafDesc* __restrict__ leaves, uint32_t n_leaves,
                          const uint64_t* __restrict__ x, const unsigned long long* __restrict__ best,
-                         uint64_t* codes, uint8_t* f_key, uint64_t* f_mask, uint32_t* err) {
+                         uint64_t* codes, uint8_t* f_key, uint64_t* f_mask, uint32_t* err,
+                         uint32_t leaf_mode) {
   const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n_leaves) return;
   const LeafDesc d = leaves[l];
@@ -524,13 +525,12 @@ __global__ void k_orient(const LeafDesc* __restrict__ leaves, uint32_t n_leaves,
     return;
   }
   if (codes != nullptr && d.code_idx != kNoCode) codes[d.code_idx] = s;
-  const uint64_t c = mix64(kLeafSalt + s);
   uint8_t e0[kMaxLeaf], e1[kMaxLeaf], stack[kMaxLeaf];
   uint64_t inc[kMaxLeaf];
   for (uint32_t v = 0; v < m; v++) inc[v] = 0;
   for (uint32_t e = 0; e < m; e++) {
     uint32_t h0, h1;
-    leaf_cells(x[d.key_off + e], c, m, &h0, &h1);
+    value_cells(leaf_mode, x[d.key_off + e], s, m, &h0, &h1);
     e0[e] = (uint8_t)h0;
     e1[e] = (uint8_t)h1;
     inc[h0] |= 1ull << e;
@@ -584,10 +584,10 @@ __global__ void k_orient(const LeafDesc* __restrict__ leaves, uint32_t n_leaves,
 
 shk_status launch_orient(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves, const uint64_t* x,
                          const unsigned long long* best, uint64_t* codes, uint8_t* f_key,
-                         uint64_t* f_mask, uint32_t* err) {
+                         uint64_t* f_mask, uint32_t* err, uint32_t leaf_mode) {
   if (n_leaves == 0) return SHK_OK;
   k_orient<<<(n_leaves + 127) / 128, 128, 0, c.stream>>>(leaves, n_leaves, x, best, codes, f_key,
-                                                         f_mask, err);
+                                                         f_mask, err, leaf_mode);
   c.launches++;
   SHK_CUDA(cudaGetLastError());
   return SHK_OK;

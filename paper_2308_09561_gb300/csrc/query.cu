@@ -16,7 +16,7 @@ struct QueryView {
   const uint64_t* O;
   const uint64_t* shard_off;
   uint64_t B;
-  uint32_t n, S, eps_num;
+  uint32_t n, S, eps_num, leaf_mode;
 };
 
 __device__ __forceinline__ uint64_t window64(const uint64_t* w, uint64_t nwords, uint64_t p) {
@@ -88,7 +88,7 @@ __device__ uint64_t query_one(const QueryView& q, uint64_t lo, uint64_t hi) {
   if (m >= 2) {
     const uint64_t seed = rice_next(q, &pos, rice_k_leaf(m));
     uint32_t h0, h1;
-    leaf_cells(lo, mix64(kLeafSalt + seed), m, &h0, &h1);
+    value_cells(q.leaf_mode, lo, seed, m, &h0, &h1);
     const uint64_t sh = b / q.S;
     const uint64_t b0 = sh * q.S, b1 = b0 + q.S < q.B ? b0 + q.S : q.B;
     const uint64_t ms = shard_slots(q.K[b1] - q.K[b0], q.eps_num);
@@ -123,6 +123,7 @@ shk_status launch_query(Ctx& c, const shk_mphf* mp, const uint64_t* lo, const ui
   q.n = (uint32_t)mp->hdr[2];
   q.S = (uint32_t)mp->hdr[5];
   q.eps_num = (uint32_t)mp->hdr[6];
+  q.leaf_mode = (uint32_t)mp->hdr[14];
   uint64_t blocks = (n + 255) / 256;
   if (blocks > (uint64_t)c.num_sms * 16) blocks = (uint64_t)c.num_sms * 16;
   k_query<<<(unsigned)blocks, 256, 0, c.stream>>>(q, lo, hi, n, ranks);

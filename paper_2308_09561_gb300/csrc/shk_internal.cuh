@@ -24,6 +24,7 @@ constexpr uint64_t kRetSalt = 0xC0AC29B7C97C50DDull;
 constexpr uint64_t kRetSalt2 = 0x3F84D5B5B5470917ull;
 constexpr uint64_t kStrSaltA = 0x9216D5D98979FB1Bull;
 constexpr uint64_t kStrSaltB = 0xD1310BA698DFB5ACull;
+constexpr uint64_t kRfSalt = 0x2FFD72DBD01ADFB7ull;  // rotation fitting: set split
 constexpr uint64_t kMagic = 0x31303053524B4853ull;  // "SHKRS001"
 constexpr uint32_t kHeaderWords = 16;
 constexpr uint32_t kMaxLeaf = 64;
@@ -129,6 +130,34 @@ __host__ __device__ __forceinline__ void leaf_cells(uint64_t x, uint64_t c, uint
   const uint32_t t = (uint32_t)(((uint64_t)(uint32_t)w * (m - 1)) >> 32);
   *h0 = u;
   *h1 = t + (t >= u ? 1u : 0u);
+}
+
+// Rotation fitting (Sec. 4; partial hash calculation, App. A.2): the cells of
+// key x under candidate v = s*m + r.  Keys of set A (top bit of
+// mix(x ^ kRfSalt) clear) take the cells of seed s - (s mod 8) when m > 32, of
+// seed s otherwise; keys of set B the cells of seed s moved by r (mod m).
+__host__ __device__ __forceinline__ void rf_cells(uint64_t x, uint64_t v, uint32_t m,
+                                                  uint32_t* h0, uint32_t* h1) {
+  const uint64_t s = v / m;
+  const uint32_t r = (uint32_t)(v - s * m);
+  if ((mix64(x ^ kRfSalt) >> 63) == 0) {
+    const uint64_t sa = m > 32 ? s - s % 8 : s;
+    leaf_cells(x, mix64(kLeafSalt + sa), m, h0, h1);
+  } else {
+    leaf_cells(x, mix64(kLeafSalt + s), m, h0, h1);
+    *h0 = *h0 + r >= m ? *h0 + r - m : *h0 + r;
+    *h1 = *h1 + r >= m ? *h1 + r - m : *h1 + r;
+  }
+}
+
+// Cells of a leaf key under its stored value (a seed, or v with rotation
+// fitting).
+__host__ __device__ __forceinline__ void value_cells(uint32_t leaf_mode, uint64_t x, uint64_t value,
+                                                     uint32_t m, uint32_t* h0, uint32_t* h1) {
+  if (leaf_mode)
+    rf_cells(x, value, m, h0, h1);
+  else
+    leaf_cells(x, mix64(kLeafSalt + value), m, h0, h1);
 }
 
 // Retrieval row of one key in a shard of m slots with shard seed r.

@@ -277,3 +277,52 @@ def test_leaf_search_graph_replay_reads_new_contents(pkg, orc):
         assert np.array_equal(seeds.cpu().numpy().view(np.uint64), want_s)
         assert np.array_equal(fm.cpu().numpy().view(np.uint64), want_f)
     assert pkg.shk_leaf_graph_replays() == r0 + 3
+
+
+RF_CASES = [(10000, 32, 2000), (5000, 24, 800), (3000, 36, 1000), (4000, 48, 2000), (777, 40, 2000),
+            (2, 2, 2), (129, 16, 16), (300, 40, 300), (2500, 8, 100)]
+
+
+@pytest.mark.parametrize("N,n,b", RF_CASES)
+@pytest.mark.parametrize("sched", [0, 1])
+def test_rotation_fitting_build_bytes_equal_oracle(pkg, orc, N, n, b, sched):
+    """Leaf mode 1 (rotation fitting with partial hash calculation)."""
+    keys = inp.distinct_u64(N, 400 + N)
+    m = pkg.shk_build(_dev(keys), n, b, sched=sched, leaf_mode=pkg.SHK_LEAF_ROTATION)
+    got = m.serialize()
+    want = orc.build_mphf(keys, n=n, b=b, leaf_mode=1)
+    assert got == want
+    lo, hi = orc.fingerprints_u64(keys)
+    ranks = m.query(_dev(keys)).cpu().numpy().view(np.uint64)
+    assert np.array_equal(ranks, orc.query(want, lo, hi))
+    assert _bijective(ranks, N)
+    m2 = pkg.shk_deserialize(got)
+    assert np.array_equal(m2.query(_dev(keys)).cpu().numpy().view(np.uint64), ranks)
+
+
+def test_rotation_fitting_million_keys_sampled(pkg, orc):
+    """10^6 keys, n = 48, rotation fitting: bijection over all keys and the
+    codes of sampled buckets equal the oracle's."""
+    import torch
+
+    N, n, b = 1_000_000, 48, 2000
+    keys = inp.distinct_u64(N, 2)
+    dk = _dev(keys)
+    m = pkg.shk_build(dk, n, b, leaf_mode=pkg.SHK_LEAF_ROTATION)
+    blob = m.serialize()
+    ranks = m.query(dk)
+    srt, _ = torch.sort(ranks)
+    assert torch.equal(srt, torch.arange(N, device="cuda", dtype=torch.int64))
+    bl = Blob(blob)
+    assert bl.h["leaf_mode"] == 1
+    B = bl.h["B"]
+    K, O = bl.K(), bl.O()
+    lo, hi = orc.fingerprints_u64(keys)
+    order = np.lexsort((lo, hi))
+    for i in (0, 211, B - 1):
+        sel = order[K[i]:K[i + 1]]
+        seeds, ks, _, _, _ = orc.bucket_build(lo[sel], hi[sel], n, rf=True)
+        codes, end = bl.rice_codes(int(O[i]), [int(k) for k in ks])
+        assert codes == [int(s) for s in seeds] and end == O[i + 1]
+    samp = np.arange(0, N, 101)
+    assert np.array_equal(orc.query(blob, lo[samp], hi[samp]), ranks.cpu().numpy().view(np.uint64)[samp])
