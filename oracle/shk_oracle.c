@@ -160,14 +160,15 @@ static uint32_t part_size(uint32_t m, uint32_t unit, uint32_t fanout, uint32_t j
 }
 
 /* Split hash (reading): g = mix(SPLIT_SALT + m), d = mix(g + s),
- * v = floor(hi32(mix(x ^ d)) * m / 2^32); the child is the number of part
- * boundaries j*unit (1 <= j < fanout) that v has reached. */
+ * a = (hi32(x) ^ lo32(d)) * (lo32(x) | 1) + hi32(d) mod 2^32,
+ * v = floor(a * m / 2^32); the child is the number of part boundaries
+ * j*unit (1 <= j < fanout) that v has reached. */
 uint32_t orc_split_child(uint64_t x, uint64_t seed, uint32_t m, uint32_t unit,
                          uint32_t fanout) {
   uint64_t g = orc_mix64(SPLIT_SALT + m);
   uint64_t d = orc_mix64(g + seed);
-  uint64_t h = orc_mix64(x ^ d);
-  uint32_t v = (uint32_t)(((h >> 32) * (uint64_t)m) >> 32);
+  uint32_t a = ((uint32_t)(x >> 32) ^ (uint32_t)d) * ((uint32_t)x | 1u) + (uint32_t)(d >> 32);
+  uint32_t v = (uint32_t)(((uint64_t)a * m) >> 32);
   uint32_t child = 0;
   for (uint32_t j = 1; j < fanout; j++)
     if (v >= j * unit) child++;

@@ -73,9 +73,9 @@ __device__ uint64_t query_one(const QueryView& q, uint64_t lo, uint64_t hi) {
   SplitShape s;
   while (split_shape(m, q.n, &s)) {
     const uint64_t seed = rice_next(q, &pos, rice_k_split(m, q.n));
-    const uint64_t g = mix64(kSplitSalt + m);
-    const uint64_t h = mix64(lo ^ mix64(g + seed));
-    const uint32_t v = __umulhi((uint32_t)(h >> 32), m);
+    const uint64_t d = mix64(mix64(kSplitSalt + m) + seed);
+    const uint32_t a = ((uint32_t)(lo >> 32) ^ (uint32_t)d) * ((uint32_t)lo | 1u) + (uint32_t)(d >> 32);
+    const uint32_t v = __umulhi(a, m);
     uint32_t child = 0;
     for (uint32_t j = 1; j < s.fanout; j++) child += v >= j * s.unit;
     for (uint32_t j = 0; j < child; j++) {

@@ -11,7 +11,43 @@
 
 namespace shk {
 
-constexpr int kRibbonThreads = 256;
+constexpr int kRibbonThreads = 1024;
+constexpr uint32_t kRegions = kRibbonThreads / 32;  // one elimination region per warp
+
+__device__ __forceinline__ uint32_t ctz64(uint64_t v) {  // v != 0
+  const uint32_t lo = (uint32_t)v;
+  return lo ? (uint32_t)__ffs((int)lo) - 1 : 31u + (uint32_t)__ffs((int)(v >> 32));
+}
+
+// Reduce one row against the table until it lands on a free slot (returns 1),
+// vanishes (returns 1 if consistent, 0 if not) or reaches slot `limit`
+// (returns 2; *st, *cf, *bv then hold the partly reduced row).
+__device__ __forceinline__ int eliminate(uint64_t* rows, uint8_t* rhs, uint32_t* st, uint64_t* cf,
+                                         uint8_t* bv, uint32_t limit) {
+  uint32_t s = *st;
+  uint64_t c = *cf;
+  uint8_t b = *bv;
+  for (;;) {
+    if (s >= limit) {
+      *st = s;
+      *cf = c;
+      *bv = b;
+      return 2;
+    }
+    const uint64_t row = rows[s];
+    if (row == 0) {
+      rows[s] = c;
+      rhs[s] = b;
+      return 1;
+    }
+    c ^= row;
+    b ^= rhs[s];
+    if (c == 0) return b ? 0 : 1;
+    const uint32_t tz = ctz64(c);
+    c >>= tz;
+    s += tz;
+  }
+}
 
 __global__ void k_shard_slots(const uint32_t* K, uint64_t B, uint32_t S, uint32_t eps_num,
                               uint64_t num_shards, uint64_t* slots) {
@@ -90,40 +126,58 @@ __global__ void __launch_bounds__(kRibbonThreads)
         pbit[i] = f[k0 + i];
       }
     }
-    __syncthreads();
     if (threadIdx.x == 0) {
+      ok_s = 1;
+      seed_s = r;
+    }
+    __syncthreads();
+    if (PRE) {
+      // Phase 1: lane 0 of every warp eliminates, in parallel with the other
+      // warps, the rows that start in its own slot range; a row that would
+      // step past its range is parked: bit 1 of its pbit is set, its start and
+      // coefficient stay as they were (other warps read them), and phase 2
+      // reduces it again from the start.  No slot and no row is written by
+      // two warps.
+      if ((threadIdx.x & 31) == 0) {
+        const uint32_t reg = threadIdx.x >> 5;
+        const uint32_t w = (uint32_t)((m + kRegions - 1) / kRegions);
+        const uint32_t r0 = reg * w, r1 = r0 + w < m ? r0 + w : (uint32_t)m;
+        int ok = 1;
+        for (uint32_t i = 0; i < keys && ok; i++) {
+          uint32_t st = pstart[i];
+          if (st < r0 || st >= r1) continue;
+          uint64_t cf = pcoef[i];
+          uint8_t bv = pbit[i];
+          const int res = eliminate(rows, rhs, &st, &cf, &bv, r1);
+          if (res == 0) ok = 0;
+          if (res == 2) pbit[i] |= 2;
+        }
+        if (!ok) ok_s = 0;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0 && ok_s) {
+      // Phase 2 (or the whole elimination without row precomputation): one
+      // thread over the whole table.
       int ok = 1;
       for (uint32_t i = 0; i < keys && ok; i++) {
-        uint64_t st, cf;
+        uint32_t st;
+        uint64_t cf;
         uint8_t bv;
         if (PRE) {
+          if (!(pbit[i] & 2)) continue;
           st = pstart[i];
           cf = pcoef[i];
-          bv = pbit[i];
+          bv = pbit[i] & 1;
         } else {
-          ribbon_row(lo[k0 + i], hi[k0 + i], r, m, &st, &cf);
+          uint64_t st64;
+          ribbon_row(lo[k0 + i], hi[k0 + i], r, m, &st64, &cf);
+          st = (uint32_t)st64;
           bv = f[k0 + i];
         }
-        for (;;) {
-          const uint64_t row = rows[st];
-          if (row == 0) {
-            rows[st] = cf;
-            rhs[st] = bv;
-            break;
-          }
-          cf ^= row;
-          bv ^= rhs[st];
-          if (cf == 0) {
-            if (bv) ok = 0;
-            break;
-          }
-          const uint32_t tz = __ffsll((long long)cf) - 1;
-          cf >>= tz;
-          st += tz;
-        }
+        if (eliminate(rows, rhs, &st, &cf, &bv, 0xFFFFFFFFu) == 0) ok = 0;
       }
       ok_s = ok;
-      seed_s = r;
     }
     __syncthreads();
     if (ok_s) break;

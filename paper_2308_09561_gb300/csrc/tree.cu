@@ -57,10 +57,15 @@ shk_status launch_tree_count(Ctx& c, const uint32_t* K, uint64_t B, uint32_t n,
 // ---------------------------------------------------------------------------
 constexpr int kSplitThreads = 256;
 
+// Split hash: a = (hi32(x) ^ lo32(d)) * (lo32(x) | 1) + hi32(d), v = hi32(a * m).
+__device__ __forceinline__ uint32_t split_value(uint64_t x, uint64_t d, uint32_t m) {
+  const uint32_t a = ((uint32_t)(x >> 32) ^ (uint32_t)d) * ((uint32_t)x | 1u) + (uint32_t)(d >> 32);
+  return __umulhi(a, m);
+}
+
 __device__ __forceinline__ uint32_t split_child_dev(uint64_t x, uint64_t d, uint32_t m,
                                                     uint32_t t1, uint32_t t2, uint32_t t3) {
-  const uint64_t h = mix64(x ^ d);
-  const uint32_t v = __umulhi((uint32_t)(h >> 32), m);
+  const uint32_t v = split_value(x, d, m);
   return (uint32_t)(v >= t1) + (uint32_t)(v >= t2) + (uint32_t)(v >= t3);
 }
 
@@ -164,8 +169,7 @@ __global__ void __launch_bounds__(kSplitThreads)
       const uint64_t d = mix64(g + s);
       uint32_t c1 = 0, c2 = 0, c3 = 0;
       for (uint32_t j = 0; j < m; j++) {
-        const uint64_t h = mix64(lo[off + j] ^ d);
-        const uint32_t v = __umulhi((uint32_t)(h >> 32), m);
+        const uint32_t v = split_value(lo[off + j], d, m);
         c1 += v >= t1;
         c2 += v >= t2;
         c3 += v >= t3;

@@ -172,3 +172,40 @@ def test_bits_per_key_breakdown(orc):
     leaf_bits = h["rice_bits"] / N
     lower = (n * math.log2(n) - math.lgamma(n + 1) / math.log(2)) / n - 1
     assert lower < leaf_bits < lower + 0.25
+
+
+def _preorder_kinds(orc, m, n):
+    """Preorder list of (is_leaf, size) for the codes of a node of m keys."""
+    sh = orc.split_shape(m, n)
+    if sh is None:
+        return [(True, m)] if m >= 2 else []
+    unit, fan = sh
+    out = [(False, m)]
+    for j in range(fan):
+        out += _preorder_kinds(orc, unit if j < fan - 1 else m - (fan - 1) * unit, n)
+    return out
+
+
+def test_leaves_made_by_splits_behave_like_random_leaves(orc):
+    """Leaf seeds inside builds (keys chosen by split hashes) have the same
+    mean number of trials as independent random leaves: 1/P(pseudoforest) of
+    uniformly random loop-free graphs on 16 cells, 33.04 (Monte Carlo, 4e8)."""
+    N, n, b = 240000, 16, 400
+    keys = inp.distinct_u64(N, 4242)
+    lo, hi = orc.fingerprints_u64(keys)
+    B = (N + b - 1) // b
+    bkt = np.array((hi.astype(object) * B) >> 64, dtype=np.int64)
+    order = np.lexsort((lo, hi))
+    K = np.zeros(B + 1, np.int64)
+    np.cumsum(np.bincount(bkt, minlength=B), out=K[1:])
+    trials = []
+    for i in range(B):
+        sel = order[K[i]:K[i + 1]]
+        seeds, _, _, _, _ = orc.bucket_build(lo[sel], hi[sel], n)
+        kinds = _preorder_kinds(orc, int(sel.size), n)
+        assert len(kinds) == seeds.size
+        trials += [int(s) + 1 for s, (leaf, m) in zip(seeds, kinds) if leaf and m == n]
+    t = np.array(trials, np.float64)
+    se = t.std() / math.sqrt(t.size)
+    assert t.size > 12000
+    assert abs(t.mean() - 33.04) < 5 * se + 0.2
