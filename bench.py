@@ -172,7 +172,7 @@ def run_ours(args):
     import torch
 
     global N_KEYS
-    N_KEYS = args.keys
+    N_KEYS = args.keys or N_KEYS
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     dist = None
@@ -321,43 +321,64 @@ def run_leafbatch(args):
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     pkg.load_library()
-    count = 65536 if args.keys == N_KEYS else args.keys
+    count = args.keys or 65536
     keys, offs = shk_inputs.leaf_instances(count, 3 + 1000 * rank)
     dk = torch.from_numpy(keys.view(np.int64)).cuda()
     off = torch.from_numpy(offs.view(np.int32)).cuda()
     seeds = torch.empty(count, dtype=torch.int64, device="cuda")
     fm = torch.empty(count, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
+    rf = args.leaf_mode == "rf" and args.workload_leafbatch_rf
     for _ in range(max(args.warmup, 0)):
-        pkg.shk_leaf_search(dk, off, 0, seeds_out=seeds, f_out=fm)
+        if rf:
+            pkg.shk_leaf_search_rf(dk, off)
+        else:
+            pkg.shk_leaf_search(dk, off, 0, seeds_out=seeds, f_out=fm)
     torch.cuda.synchronize()
     r0 = pkg.shk_leaf_graph_replays()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         for i in range(args.steps):
             ev[i][0].record(stream)
-            pkg.shk_leaf_search(dk, off, 0, seeds_out=seeds, f_out=fm)
+            if rf:
+                seeds, fm = pkg.shk_leaf_search_rf(dk, off)
+            else:
+                pkg.shk_leaf_search(dk, off, 0, seeds_out=seeds, f_out=fm)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     s = seeds.cpu().numpy().view(np.uint64).astype(np.float64)
     sizes = np.diff(offs.astype(np.int64))
-    seeds_min = float((s + 1).sum())
+    seeds_min = float((s + 1).sum())  # with rotation fitting: candidates v + 1
     evals = float(((s + 1) * sizes).sum())
     peaks = _peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak = sms * 4 * 32 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    ach = evals * OPS_PER_EVAL_WIDE / (t / args.steps) / 1e12
-    line = {"metric": "batched leaf search: leaf seeds tested/s (65,536 leaves, m in [40,64])",
+    if rf:
+        # rotation fitting: seeds s = 0 .. floor(v / m) are tested; each seed
+        # hashes the keys of set B (m / 2 expected) and, once per 8 seeds,
+        # those of set A.  Only the hash evaluations are counted (the rotation
+        # intersection is left out), so this is a lower bound on the work.
+        tested = np.floor(s / sizes) + 1
+        hashes = float((tested * sizes * (0.5 + 0.5 / 8)).sum())
+        ach = hashes * OPS_PER_EVAL_WIDE / (t / args.steps) / 1e12
+        kernel = "k_leaf_rf_persistent"
+    else:
+        ach = evals * OPS_PER_EVAL_WIDE / (t / args.steps) / 1e12
+        kernel = "k_leaf_persistent"
+    line = {"metric": "batched leaf search: leaf seeds (rotation fitting: candidates) tested/s "
+                      "(65,536 leaves, m in [40,64])",
+            "leaf_mode": "rf" if rf else "plain",
             "value": seeds_min * args.steps / t, "unit": "seeds/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "dtype": "u64", "data": "synthetic",
             "config": {"workload": "leaf_batch_65536_leaves_m40_64", "leaves": count, "seed_stream": 3},
             "key_seed_evals_per_s": evals * args.steps / t, "mean_seed": float(s.mean()),
             "graph_replays": pkg.shk_leaf_graph_replays() - r0,
-            "tuned_cfg": pkg.shk_leaf_tune(64),
-            "roofline": {"bound": "alu", "kernel": "k_leaf_persistent", "achieved": ach, "peak": peak,
+            "roofline": {"bound": "alu", "kernel": kernel, "achieved": ach, "peak": peak,
                          "unit": "T int-lane-ops/s", "frac": ach / peak}}
+    if not rf:
+        line["tuned_cfg"] = pkg.shk_leaf_tune(64)
     clocks = clk.summary()
     if clocks:
         line["clocks"] = clocks
@@ -442,6 +463,74 @@ def run_serve(args):
     return 0
 
 
+def run_strings(args):
+    """10^8 random strings (length uniform in [10, 50], bytes uniform in
+    [1, 127], stream seed 4) hashed to 128-bit fingerprints, leaf size 64,
+    bucket size 2000, rotation fitting with partial hash calculation.  One
+    timed build (after a warm-up build of the first 10^6 strings), then every
+    key is queried and the ranks checked to be a permutation of [0, N)."""
+    import torch
+
+    import paper_2308_09561_gb300 as pkg
+    import shk_inputs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pkg.load_library()
+    count = args.keys or 100_000_000
+    t = time.perf_counter()
+    data, offs = shk_inputs.ascii_strings(count, 4 + 1000 * rank)
+    gen_s = time.perf_counter() - t
+    ddata = torch.from_numpy(data).cuda()
+    doffs = torch.from_numpy(offs.view(np.int64)).cuda()
+    leaf, mode = 64, (pkg.SHK_LEAF_ROTATION if args.leaf_mode == "rf" else pkg.SHK_LEAF_PLAIN)
+    w = min(count, 1_000_000)
+    pkg.shk_build(ddata, leaf, BUCKET, kind=pkg.SHK_KEYS_STR, str_offsets=doffs[:w + 1], leaf_mode=mode).close()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        m = pkg.shk_build(ddata, leaf, BUCKET, kind=pkg.SHK_KEYS_STR, str_offsets=doffs, leaf_mode=mode,
+                          profile=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = m.stats()
+    blob = m.serialize()
+    tq = time.perf_counter()
+    ranks = m.query(ddata, kind=pkg.SHK_KEYS_STR, str_offsets=doffs)
+    torch.cuda.synchronize()
+    query_s = time.perf_counter() - tq
+    srt, _ = torch.sort(ranks)
+    bij = bool(torch.equal(srt, torch.arange(count, device="cuda", dtype=torch.int64)))
+    del srt, ranks
+    m.close()
+    # fingerprint + partition bytes: read the strings and their offsets, write
+    # fingerprints and bucket ids, then the scatter and the in-bucket sort
+    # each read and write 16 bytes per key (plus the 4-byte bucket id read)
+    part_bytes = data.size + 8 * (count + 1) + 20 * count + (20 + 16) * count + 32 * count
+    part_ms = st["ms_fingerprint"] + st["ms_partition"]
+    line = {"metric": "MPHF build keys/s, 10^8 string keys, leaf 64", "value": count / (ms / 1e3),
+            "unit": "keys/s", "n_gpus": ws, "steps": 1, "warmup": 1, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "mphf_build_1e8_strings_leaf64_bucket2000", "keys": count,
+                       "string_bytes": int(data.size), "leaf_size": leaf, "bucket_size": BUCKET,
+                       "leaf_mode": args.leaf_mode},
+            "bits_per_key": 8 * len(blob) / count, "bijection": bij, "query_s_all_keys": query_s,
+            "phase_ms": {k: st[k] for k in ("ms_fingerprint", "ms_partition", "ms_split", "ms_leaf",
+                                            "ms_orient", "ms_encode", "ms_ribbon", "ms_total")},
+            "partition_gbs": part_bytes / (part_ms / 1e3) / 1e9,
+            "leaf_candidates_per_s": st["leaf_seeds_min"] / (st["ms_leaf"] / 1e3),
+            "leaves": st["n_leaves"], "input_generation_s": gen_s}
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,11 +538,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--keys", type=int, default=N_KEYS, help="smaller key counts for profiling runs")
+    ap.add_argument("--keys", type=int, default=None,
+                    help="key (leafbatch: leaf) count other than the workload's own, for profiling runs")
     ap.add_argument("--compare-per-bucket", action="store_true",
                     help="time the one-launch-per-bucket form on the whole workload (slow)")
     ap.add_argument("--requests", type=int, default=100, help="serve: number of requests")
-    ap.add_argument("--workload", default="build", choices=["build", "leafbatch", "serve"],
+    ap.add_argument("--leafbatch-rf", dest="workload_leafbatch_rf", action="store_true",
+                    help="leafbatch: rotation fitting (shk_leaf_search_rf)")
+    ap.add_argument("--leaf-mode", default="rf", choices=["rf", "plain"],
+                    help="strings / leafbatch workloads: rotation fitting or plain leaves")
+    ap.add_argument("--workload", default="build", choices=["build", "leafbatch", "serve", "strings"],
                     help="leafbatch: 65,536 independent leaves of 40..64 keys, one graph-replayed launch")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -462,6 +556,8 @@ def main():
         return run_leafbatch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "strings":
+        return run_strings(args)
     return run_ours(args)
 
 

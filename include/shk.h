@@ -202,6 +202,16 @@ shk_status shk_leaf_tune(uint32_t leaf_size, uint32_t* cfg_out, double* evals_pe
  * (as in shk_leaf_tune; passes 0); returns their number. */
 uint32_t shk_leaf_configs(uint32_t* cfgs, uint32_t cap);
 
+/* shk_leaf_search_rf -- the batched leaf search with rotation fitting and
+ * partial hash calculation (paper Sec. 4 Rotation Fitting, App. A.2): per
+ * leaf the smallest v = s*m + r whose graph is a pseudoforest, where set A's
+ * keys take the cells of seed s - (s mod 8) (m > 32; s otherwise) and set B's
+ * the cells of seed s moved by r (mod m); f as in shk_leaf_search.  Buffers
+ * and errors as for shk_leaf_search (no seed start: values start at 0). */
+shk_status shk_leaf_search_rf(const uint64_t* leaf_keys, const uint32_t* leaf_off,
+                              uint32_t n_leaves, uint64_t* values_out, uint64_t* f_out,
+                              void* cuda_stream);
+
 /* shk_leaf_graph_replays -- how many times this host thread has launched the
  * captured leaf-search graph (each shk_leaf_search call launches it once;
  * calls with unchanged pointers and sizes reuse the instantiated graph). */

@@ -27,7 +27,8 @@ SHK_LEAF_PLAIN, SHK_LEAF_ROTATION = 0, 1
 # exported symbols declared in include/shk.h
 EXPORTS = ("shk_build", "shk_build_stats", "shk_query", "shk_serialize", "shk_deserialize",
            "shk_size_bits", "shk_free", "shk_last_error", "shk_leaf_search", "shk_leaf_search_noalloc",
-           "shk_leaf_tune", "shk_leaf_configs", "shk_leaf_graph_replays", "shk_server_create",
+           "shk_leaf_tune", "shk_leaf_configs", "shk_leaf_graph_replays", "shk_leaf_search_rf",
+           "shk_server_create",
            "shk_server_submit", "shk_server_poll", "shk_server_wait", "shk_server_get_stats",
            "shk_server_destroy", "shk_version")
 
@@ -97,6 +98,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "shk_leaf_tune": (i32, [u32, vp, vp, i32, vp]),
         "shk_leaf_configs": (u32, [vp, u32]),
         "shk_leaf_graph_replays": (u64, []),
+        "shk_leaf_search_rf": (i32, [vp, vp, u32, vp, vp, vp]),
         "shk_server_create": (i32, [u64, u32, ctypes.POINTER(vp)]),
         "shk_server_submit": (i32, [vp, ctypes.POINTER(_Keys), ctypes.POINTER(_Opts), ctypes.POINTER(u64)]),
         "shk_server_poll": (i32, [vp, u64, ctypes.POINTER(vp), ctypes.POINTER(_ReqInfo)]),
@@ -393,3 +395,19 @@ def shk_server_get_stats(server: int) -> dict:
 
 def shk_server_destroy(server: int) -> None:
     load_library().shk_server_destroy(server)
+
+
+def shk_leaf_search_rf(leaf_keys, leaf_off, want_f: bool = True, stream=None):
+    """Batched leaf search with rotation fitting: (values v = s*m + r, f masks)."""
+    torch = _torch()
+    lib = load_library()
+    if not (leaf_keys.is_cuda and leaf_off.is_cuda):
+        raise ValueError("shk_leaf_search_rf takes device tensors")
+    kk = leaf_keys.contiguous()
+    off = leaf_off.contiguous()
+    nl = off.numel() - 1
+    vals = torch.empty(max(nl, 1), dtype=torch.int64, device=kk.device)
+    f = torch.empty(max(nl, 1), dtype=torch.int64, device=kk.device) if want_f else None
+    _check(lib.shk_leaf_search_rf(kk.data_ptr(), off.data_ptr(), nl, vals.data_ptr(),
+                                  f.data_ptr() if f is not None else None, _stream_handle(stream)))
+    return vals[:nl], (f[:nl] if f is not None else None)

@@ -638,6 +638,40 @@ extern "C" shk_status shk_leaf_search(const uint64_t* leaf_keys, const uint32_t*
 
 extern "C" uint64_t shk_leaf_graph_replays(void) { return g_leaf_graph.replays; }
 
+extern "C" shk_status shk_leaf_search_rf(const uint64_t* leaf_keys, const uint32_t* leaf_off,
+                                         uint32_t n_leaves, uint64_t* values_out, uint64_t* f_out,
+                                         void* cuda_stream) {
+  if (n_leaves && (!leaf_keys || !leaf_off || !values_out)) return fail(SHK_EINVAL, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Ctx c(st);
+  SHK_TRY(init_ctx(c));
+  if (n_leaves == 0) return SHK_OK;
+  auto run = [&]() -> shk_status {
+    LeafDesc* d;
+    uint32_t* err;
+    unsigned long long* counters;
+    SHK_TRY(c.arena.alloc(&d, n_leaves));
+    SHK_TRY(c.arena.alloc(&err, 1, true));
+    SHK_TRY(c.arena.alloc(&counters, 1, true));
+    k_leaf_descs<<<(n_leaves + 255) / 256, 256, 0, st>>>(leaf_off, n_leaves, d);
+    c.launches++;
+    SHK_CUDA(cudaGetLastError());
+    SHK_CUDA(cudaMemsetAsync(values_out, 0xFF, (size_t)n_leaves * 8, st));
+    LeafSearchArgs a{d, n_leaves, leaf_keys, 0, (unsigned long long*)values_out, err, counters,
+                     LeafCfg{8, 8, 2, 2}};
+    SHK_TRY(launch_leaf_rf_persistent(c, a));
+    SHK_TRY(launch_orient(c, d, n_leaves, leaf_keys, (unsigned long long*)values_out, nullptr,
+                          nullptr, f_out, err, SHK_LEAF_ROTATION));
+    uint32_t h_err = 0;
+    SHK_CUDA(cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, st));
+    SHK_CUDA(cudaStreamSynchronize(st));
+    return device_errors(h_err);
+  };
+  const shk_status s = run();
+  if (s != SHK_OK) cudaStreamSynchronize(st);
+  return s;
+}
+
 extern "C" shk_status shk_leaf_tune(uint32_t leaf_size, uint32_t* cfg_out, double* evals_per_s,
                                     int probe_all, double* all_evals_per_s) {
   if (leaf_size < 2 || leaf_size > kMaxLeaf || !cfg_out) return fail(SHK_EINVAL, "bad argument");

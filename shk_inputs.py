@@ -64,13 +64,18 @@ def leaf_instances(count: int, seed: int, lo: int = 40, hi: int = 64):
     return keys, offs.astype(np.uint32)
 
 
-def ascii_strings(count: int, seed: int, min_len: int = 10, max_len: int = 50):
-    """(bytes, offsets) of ``count`` random strings, bytes uniform in [1, 127]."""
+def ascii_strings(count: int, seed: int, min_len: int = 10, max_len: int = 50,
+                  chunk: int = 1 << 26):
+    """(bytes, offsets) of ``count`` random strings, bytes uniform in [1, 127].
+    Generated in chunks of ``chunk`` bytes (same values for any chunk size)."""
     span = max_len - min_len + 1
     lens = min_len + np.floor(uniform01(seed, count) * span).astype(np.int64)
     offs = np.zeros(count + 1, np.uint64)
     np.cumsum(lens, out=offs[1:].view(np.int64))
     total = int(offs[-1])
-    raw = splitmix64_stream(seed, total, start=count + 1)
-    data = (1 + (raw % np.uint64(127))).astype(np.uint8)
+    data = np.empty(total, np.uint8)
+    for a in range(0, total, chunk):
+        n = min(chunk, total - a)
+        raw = splitmix64_stream(seed, n, start=count + 1 + a)
+        data[a:a + n] = (1 + (raw % np.uint64(127))).astype(np.uint8)
     return data, offs

@@ -326,3 +326,14 @@ def test_rotation_fitting_million_keys_sampled(pkg, orc):
         assert codes == [int(s) for s in seeds] and end == O[i + 1]
     samp = np.arange(0, N, 101)
     assert np.array_equal(orc.query(blob, lo[samp], hi[samp]), ranks.cpu().numpy().view(np.uint64)[samp])
+
+
+@pytest.mark.parametrize("count,seed,lo_m,hi_m", [(2000, 81, 1, 40), (12, 82, 56, 64), (300, 83, 33, 48)])
+def test_rotation_fitting_leaf_search_equals_oracle(pkg, orc, count, seed, lo_m, hi_m):
+    import torch
+
+    keys, offs = inp.leaf_instances(count, seed, lo_m, hi_m)
+    want_v, want_f = orc.leaf_search_batch(keys, offs, 0, rf=True)
+    v, f = pkg.shk_leaf_search_rf(_dev(keys), torch.from_numpy(offs.view(np.int32)).cuda())
+    assert np.array_equal(v.cpu().numpy().view(np.uint64), want_v)
+    assert np.array_equal(f.cpu().numpy().view(np.uint64), want_f)
