@@ -22,7 +22,6 @@ namespace shk {
 
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
 constexpr int kRfSeeds = 8;  // seeds per lane (= the partial-hash period)
-constexpr uint32_t kRfPartialK = 8;
 
 struct RfScratch {
   uint64_t x[kMaxLeaf];  // leaf inputs (multiplier bit set), set A first
@@ -57,6 +56,90 @@ __device__ __forceinline__ uint64_t rf_rotations(uint64_t ma, uint64_t mb, uint3
     if (r == 0) break;
   }
   return r;
+}
+
+// 64-bit rotation left by k (0 <= k < 64) from two funnel shifts
+__device__ __forceinline__ uint64_t rot64(uint64_t v, uint32_t k) {
+  const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+  const uint32_t a = (k & 32) ? hi : lo, b = (k & 32) ? lo : hi;
+  return ((uint64_t)__funnelshift_l(a, b, k) << 32) | __funnelshift_l(b, a, k);
+}
+
+// Valid rotations of the 8 seeds of a lane that share the set-A mask ma
+// (m > 32).  First, for up to K0 cells z missed by A, every seed's set is
+// intersected with rot(reflect(B_u), z) without branches (the 8 seeds give
+// independent instruction streams and all lanes stay in step); then the few
+// rotations left are checked one by one against the remaining cells.  The
+// result is the same set as the plain intersection over all missed cells.
+template <bool M64>
+__device__ __forceinline__ void rf_rotations8(uint64_t ma, const uint64_t* mb, uint32_t m,
+                                              uint64_t full, uint64_t* rot) {
+  uint64_t z;
+  if (M64) {
+    // the 64 cells as two 32-bit halves: a rotation by c < 32 (cells of the
+    // low half) or by 32 + c (high half) is a pair of funnel shifts
+    constexpr int kHalf = 12;
+    uint32_t zl = ~(uint32_t)ma, zh = ~(uint32_t)(ma >> 32);
+    uint32_t rl[kRfSeeds], rh[kRfSeeds], bl[kRfSeeds], bh[kRfSeeds];
+#pragma unroll
+    for (int u = 0; u < kRfSeeds; u++) {
+      const uint64_t b = rot64(__brevll(mb[u]), 1);  // reflect: bit b -> bit (64 - b) mod 64
+      bl[u] = (uint32_t)b;
+      bh[u] = (uint32_t)(b >> 32);
+      rl[u] = ~0u;
+      rh[u] = ~0u;
+    }
+    for (int it = 0; it < kHalf && zl; it++) {
+      const uint32_t c = __ffs(zl) - 1;
+      zl &= zl - 1;
+#pragma unroll
+      for (int u = 0; u < kRfSeeds; u++) {
+        rh[u] &= __funnelshift_l(bl[u], bh[u], c);
+        rl[u] &= __funnelshift_l(bh[u], bl[u], c);
+      }
+    }
+    for (int it = 0; it < kHalf && zh; it++) {
+      const uint32_t c = __ffs(zh) - 1;
+      zh &= zh - 1;
+#pragma unroll
+      for (int u = 0; u < kRfSeeds; u++) {
+        rh[u] &= __funnelshift_l(bh[u], bl[u], c);
+        rl[u] &= __funnelshift_l(bl[u], bh[u], c);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kRfSeeds; u++) rot[u] = ((uint64_t)rh[u] << 32) | rl[u];
+    z = ((uint64_t)zh << 32) | zl;
+  } else {
+    constexpr int kSteps = 20;
+    z = ~ma & full;
+    uint64_t bh[kRfSeeds];
+#pragma unroll
+    for (int u = 0; u < kRfSeeds; u++) {
+      bh[u] = reflectm(mb[u], m, full);
+      rot[u] = full;
+    }
+    for (int it = 0; it < kSteps && z; it++) {
+      const uint32_t c = __ffsll((long long)z) - 1;
+      z &= z - 1;
+#pragma unroll
+      for (int u = 0; u < kRfSeeds; u++) rot[u] &= rotm(bh[u], c, m, full);
+    }
+  }
+  if (z) {
+    // rotation r survives iff every remaining missed cell is in rot(B, r)
+#pragma unroll
+    for (int u = 0; u < kRfSeeds; u++) {
+      uint64_t rr = rot[u], keep = 0;
+      while (rr) {
+        const uint32_t r = __ffsll((long long)rr) - 1;
+        rr &= rr - 1;
+        const uint64_t moved = M64 ? rot64(mb[u], r) : rotm(mb[u], r, m, full);
+        if ((z & ~moved) == 0) keep |= 1ull << r;
+      }
+      rot[u] = keep;
+    }
+  }
 }
 
 __device__ __forceinline__ uint32_t add_mod(uint32_t h, uint32_t r, uint32_t m) {
@@ -252,12 +335,18 @@ __device__ uint64_t search_rf(RfScratch* ws, uint32_t m, uint32_t na, uint64_t s
       }
     }
     uint64_t rot[kRfSeeds];
+    if (WIDE) {
+      if (m == 64)
+        rf_rotations8<true>(ma[0], mb, m, full, rot);
+      else
+        rf_rotations8<false>(ma[0], mb, m, full, rot);
+    } else {
+#pragma unroll
+      for (int u = 0; u < kRfSeeds; u++) rot[u] = rf_rotations(ma[u], mb[u], m, full);
+    }
     bool any = false;
 #pragma unroll
-    for (int u = 0; u < kRfSeeds; u++) {
-      rot[u] = rf_rotations(WIDE ? ma[0] : ma[u], mb[u], m, full);
-      any |= rot[u] != 0;
-    }
+    for (int u = 0; u < kRfSeeds; u++) any |= rot[u] != 0;
     uint32_t lanes = __ballot_sync(kFullMask, any);
     while (lanes) {
       const uint32_t l = __ffs(lanes) - 1;
