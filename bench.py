@@ -506,10 +506,10 @@ def run_strings(args):
     bij = bool(torch.equal(srt, torch.arange(count, device="cuda", dtype=torch.int64)))
     del srt, ranks
     m.close()
-    # fingerprint + partition bytes: read the strings and their offsets, write
-    # fingerprints and bucket ids, then the scatter and the in-bucket sort
-    # each read and write 16 bytes per key (plus the 4-byte bucket id read)
-    part_bytes = data.size + 8 * (count + 1) + 20 * count + (20 + 16) * count + 32 * count
+    # fingerprint + radix partition bytes: read the strings and their
+    # offsets, write one 16-byte fingerprint per key; the scatter reads it
+    # and writes it into its bucket
+    part_bytes = data.size + 8 * (count + 1) + 16 * count + 32 * count
     part_ms = st["ms_fingerprint"] + st["ms_partition"]
     line = {"metric": "MPHF build keys/s, 10^8 string keys, leaf 64", "value": count / (ms / 1e3),
             "unit": "keys/s", "n_gpus": ws, "steps": 1, "warmup": 1, "ms_per_step": ms,

@@ -105,7 +105,12 @@ typedef struct {
   uint64_t leaf_key_evals;      /* sum over leaves of (seed + 1) * m             */
   uint64_t kernel_launches;     /* library kernels launched by the build         */
   uint64_t size_bits;           /* shk_size_bits                                 */
-  /* phase times in milliseconds (profile = 1), CUDA events on the stream    */
+  /* phase times in milliseconds (profile = 1), CUDA events on the stream:  */
+  /* fingerprint = key staging, fingerprints and the bucket histogram;       */
+  /* partition = bucket offsets and the scatter into buckets; split = the    */
+  /* in-bucket sort and the splitting trees; leaf; orient; encode = Rice and */
+  /* Elias-Fano; ribbon = retrieval; total also holds the tree bookkeeping   */
+  /* and its host synchronisation.                                           */
   double ms_fingerprint, ms_partition, ms_split, ms_leaf, ms_orient, ms_encode,
       ms_ribbon, ms_total;
   uint64_t leaf_launches;       /* launches of the leaf-search kernel           */

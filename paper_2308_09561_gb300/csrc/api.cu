@@ -189,20 +189,20 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   SHK_TRY(stage_keys(c, keys, &kdata, &koffs));
 
   // a1: fingerprints, buckets, histogram
-  uint64_t *lo, *hi;
-  uint32_t *bkt, *counts, *err;
-  SHK_TRY(c.arena.alloc(&lo, N));
-  SHK_TRY(c.arena.alloc(&hi, N));
-  SHK_TRY(c.arena.alloc(&bkt, N));
+  ulonglong2* fp;
+  uint32_t *counts, *err;
+  SHK_TRY(c.arena.alloc(&fp, N));
   SHK_TRY(c.arena.alloc(&counts, B, true));
   SHK_TRY(c.arena.alloc(&err, 1, true));
-  SHK_TRY(launch_fingerprint(c, keys->kind, kdata, koffs, N32, B, lo, hi, bkt, counts));
+  SHK_TRY(launch_fingerprint(c, keys->kind, kdata, koffs, N32, B, fp, counts));
   const int t1 = pt.mark();
 
-  // tree shape of every bucket, prefix sums, one host sync for the sizes
+  // bucket offsets; tree shape of every bucket, prefix sums, one host sync
+  // for the sizes
   uint32_t *K, *nleaf, *ncode, *nsplit, *leaf_base, *code_base, *split_base, *maxb;
   SHK_TRY(c.arena.alloc(&K, B + 1));
   SHK_TRY((exclusive_scan<uint32_t, uint32_t>(c, counts, B, K)));
+  const int t1a = pt.mark();
   SHK_TRY(c.arena.alloc(&nleaf, B));
   SHK_TRY(c.arena.alloc(&ncode, B));
   SHK_TRY(c.arena.alloc(&nsplit, B));
@@ -214,7 +214,8 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   SHK_TRY((exclusive_scan<uint32_t, uint32_t>(c, nleaf, B, leaf_base)));
   SHK_TRY((exclusive_scan<uint32_t, uint32_t>(c, ncode, B, code_base)));
   SHK_TRY((exclusive_scan<uint32_t, uint32_t>(c, nsplit, B, split_base)));
-  uint32_t h_maxb = 0, h_L = 0, h_C = 0, h_splits = 0, h_err = 0;
+  uint32_t h_maxb = 0, h_L = 0, h_C = 0, h_splits = 0, h_err = 0, h_total = 0;
+  SHK_TRY(d2h(c, &h_total, K + B));
   SHK_TRY(d2h(c, &h_maxb, maxb));
   SHK_TRY(d2h(c, &h_L, leaf_base + B));
   SHK_TRY(d2h(c, &h_C, code_base + B));
@@ -226,12 +227,13 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   }
   SHK_CUDA(cudaStreamSynchronize(st));
   if (h_maxb > kMaxBucketKeys) return fail(SHK_EINVAL, "a bucket holds more than 8192 keys");
+  if (h_total != N) return fail(SHK_ECUDA, "bucket histogram does not add up to the key count");
 
-  // a2: partition and in-bucket sort
-  uint64_t *slo, *shi;
-  SHK_TRY(c.arena.alloc(&slo, N));
-  SHK_TRY(c.arena.alloc(&shi, N));
-  SHK_TRY(launch_partition(c, lo, hi, bkt, N32, B, K, h_maxb, slo, shi, err));
+  // a2: partition into buckets (the in-bucket sort opens the splitting kernel)
+  ulonglong2* sfp;
+  SHK_TRY(c.arena.alloc(&sfp, N));
+  const int t1b = pt.mark();
+  SHK_TRY(launch_scatter(c, fp, N32, B, K, sfp));
   const int t2 = pt.mark();
 
   // a3: splitting trees
@@ -243,8 +245,8 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   SHK_TRY(c.arena.alloc(&leaves, h_L));
   SHK_TRY(c.arena.alloc(&llo, N));
   SHK_TRY(c.arena.alloc(&lhi, N));
-  SHK_TRY(launch_split(c, slo, shi, K, B, n, h_maxb, code_base, leaf_base, codes, code_k, leaves,
-                       llo, lhi, err));
+  SHK_TRY(launch_split(c, sfp, K, B, n, h_maxb, code_base, leaf_base, codes, code_k, leaves, llo,
+                       lhi, err));
   const int t3 = pt.mark();
 
   // a4 + a5: leaf seeds
@@ -365,7 +367,7 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   s.leaf_launches = leaf_launches;
   s.size_bits = m->words * 64;
   s.ms_fingerprint = pt.ms(t0, t1);
-  s.ms_partition = pt.ms(t1, t2);
+  s.ms_partition = pt.ms(t1, t1a) + pt.ms(t1b, t2);
   s.ms_split = pt.ms(t2, t3);
   s.ms_leaf = pt.ms(t3, t4);
   s.ms_orient = pt.ms(t4, t5);

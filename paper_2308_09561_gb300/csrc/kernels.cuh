@@ -23,14 +23,12 @@ shk_status exclusive_scan(Ctx& c, const Tin* in, uint64_t n, T* out);
 
 // a1
 shk_status launch_fingerprint(Ctx& c, int kind, const void* data, const uint64_t* offs,
-                              uint32_t n_keys, uint64_t B, uint64_t* lo, uint64_t* hi,
-                              uint32_t* bkt, uint32_t* counts);
+                              uint32_t n_keys, uint64_t B, ulonglong2* fp, uint32_t* counts);
 shk_status launch_fingerprint_only(Ctx& c, int kind, const void* data, const uint64_t* offs,
                                    uint64_t n_keys, uint64_t* lo, uint64_t* hi);
 // a2
-shk_status launch_partition(Ctx& c, const uint64_t* lo, const uint64_t* hi, const uint32_t* bkt,
-                            uint32_t n_keys, uint64_t B, const uint32_t* K, uint32_t max_bucket,
-                            uint64_t* slo, uint64_t* shi, uint32_t* err);
+shk_status launch_scatter(Ctx& c, const ulonglong2* fp, uint32_t n_keys, uint64_t B,
+                          const uint32_t* K, ulonglong2* sfp);
 
 // tree bookkeeping: per bucket the number of searched leaves (m >= 2), of
 // codes (split nodes + searched leaves) and of split nodes; plus the largest
@@ -39,10 +37,10 @@ shk_status launch_tree_count(Ctx& c, const uint32_t* K, uint64_t B, uint32_t n,
                              uint32_t* n_leaves, uint32_t* n_codes, uint32_t* n_splits,
                              uint32_t* max_bucket);
 // a3
-shk_status launch_split(Ctx& c, const uint64_t* slo, const uint64_t* shi, const uint32_t* K,
-                        uint64_t B, uint32_t n, uint32_t max_bucket, const uint32_t* code_base,
-                        const uint32_t* leaf_base, uint64_t* codes, uint8_t* code_k,
-                        LeafDesc* leaves, uint64_t* llo, uint64_t* lhi, uint32_t* err);
+shk_status launch_split(Ctx& c, const ulonglong2* sfp, const uint32_t* K, uint64_t B, uint32_t n,
+                        uint32_t max_bucket, const uint32_t* code_base, const uint32_t* leaf_base,
+                        uint64_t* codes, uint8_t* code_k, LeafDesc* leaves, uint64_t* llo,
+                        uint64_t* lhi, uint32_t* err);
 
 // a4 + a5: leaf seed search.  best[L] must be preset to ~0.
 // Kernel configuration: seeds per lane, warps per block, key-loop unroll and

@@ -38,12 +38,13 @@ struct Request {
 };
 
 // Device bytes a build holds while it runs: keys staged on the device, three
-// fingerprint copies, bucket ids, orientation bits, per-leaf and per-bucket
-// arrays, the encoded result; plus a fixed allowance.
+// 16-byte fingerprint copies (hashed, partitioned once and twice), the leaf
+// order copy, orientation bits, per-leaf and per-bucket arrays, the encoded
+// result; plus a fixed allowance.
 uint64_t footprint(uint64_t n_keys, const shk_build_opts& o, uint64_t key_bytes) {
   const uint64_t b = o.bucket_size ? o.bucket_size : 1;
   const uint64_t buckets = n_keys / b + 1;
-  return key_bytes + n_keys * 64 + buckets * 96 + (8ull << 20);
+  return key_bytes + n_keys * 80 + buckets * 96 + (8ull << 20);
 }
 
 }  // namespace

@@ -95,13 +95,70 @@ __device__ uint64_t block_exclusive_scan_u64(uint64_t v) {
   return before + x - v;
 }
 
+// Sort of one bucket by (hi, lo) in shared memory.  Inside bucket b the
+// low 64 bits of hi * B grow with hi, so their top bits give sub-bins in key
+// order: a counting sort into about one sub-bin per key, then an insertion
+// sort inside each sub-bin (a handful of keys).  lo/hi/idx receive the sorted
+// keys and their positions in the bucket's input range; adjacent equal
+// fingerprints are duplicate keys.
+__device__ void sort_bucket(const ulonglong2* __restrict__ in, uint32_t size, uint64_t B,
+                           uint32_t sub_bits, uint32_t* cnt, uint64_t* lo, uint64_t* hi,
+                           uint16_t* idx, uint32_t* err) {
+  const uint32_t tid = threadIdx.x, nsub = 1u << sub_bits, sh = 64 - sub_bits;
+  for (uint32_t i = tid; i < nsub; i += kSplitThreads) cnt[i] = 0;
+  __syncthreads();
+  for (uint32_t j = tid; j < size; j += kSplitThreads) atomicAdd(&cnt[(in[j].y * B) >> sh], 1u);
+  __syncthreads();
+  // exclusive prefix sums of the sub-bin counts: thread t owns a contiguous run
+  const uint32_t per = (nsub + kSplitThreads - 1) / kSplitThreads;
+  const uint32_t i0 = tid * per < nsub ? tid * per : nsub, i1 = i0 + per < nsub ? i0 + per : nsub;
+  uint64_t run = 0;
+  for (uint32_t i = i0; i < i1; i++) run += cnt[i];
+  uint64_t pre = block_exclusive_scan_u64(run);
+  for (uint32_t i = i0; i < i1; i++) {
+    const uint32_t c = cnt[i];
+    cnt[i] = (uint32_t)pre;
+    pre += c;
+  }
+  __syncthreads();
+  for (uint32_t j = tid; j < size; j += kSplitThreads) {
+    const ulonglong2 v = in[j];
+    const uint32_t p = atomicAdd(&cnt[(v.y * B) >> sh], 1u);
+    lo[p] = v.x;
+    hi[p] = v.y;
+    idx[p] = (uint16_t)j;
+  }
+  __syncthreads();
+  // cnt[s] is now the end of sub-bin s
+  for (uint32_t sb = tid; sb < nsub; sb += kSplitThreads) {
+    const uint32_t e = cnt[sb], b0 = sb ? cnt[sb - 1] : 0;
+    for (uint32_t i = b0 + 1; i < e; i++) {
+      const uint64_t kh = hi[i], kl = lo[i];
+      const uint16_t ki = idx[i];
+      uint32_t j = i;
+      while (j > b0 && (hi[j - 1] > kh || (hi[j - 1] == kh && lo[j - 1] > kl))) {
+        hi[j] = hi[j - 1];
+        lo[j] = lo[j - 1];
+        idx[j] = idx[j - 1];
+        j--;
+      }
+      hi[j] = kh;
+      lo[j] = kl;
+      idx[j] = ki;
+    }
+  }
+  __syncthreads();
+  for (uint32_t j = tid; j + 1 < size; j += kSplitThreads)
+    if (hi[j] == hi[j + 1] && lo[j] == lo[j + 1]) atomicOr(err, kErrDup);
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kSplitThreads)
-    k_split(const uint64_t* __restrict__ slo, const uint64_t* __restrict__ shi,
-            const uint32_t* __restrict__ K, uint32_t n, uint32_t cap,
-            const uint32_t* __restrict__ code_base, const uint32_t* __restrict__ leaf_base,
-            uint64_t* __restrict__ codes, uint8_t* __restrict__ code_k,
-            LeafDesc* __restrict__ leaves, uint64_t* __restrict__ llo,
-            uint64_t* __restrict__ lhi, uint32_t* err) {
+    k_split(const ulonglong2* __restrict__ sfp, const uint32_t* __restrict__ K, uint64_t B,
+            uint32_t n, uint32_t cap, uint32_t sub_bits, const uint32_t* __restrict__ code_base,
+            const uint32_t* __restrict__ leaf_base, uint64_t* __restrict__ codes,
+            uint8_t* __restrict__ code_k, LeafDesc* __restrict__ leaves,
+            uint64_t* __restrict__ llo, uint64_t* __restrict__ lhi, uint32_t* err) {
   extern __shared__ uint64_t smem[];
   const uint32_t b = blockIdx.x;
   const uint32_t start = K[b], size = K[b + 1] - start;
@@ -110,6 +167,7 @@ __global__ void __launch_bounds__(kSplitThreads)
   uint64_t* tlo = lo + cap;
   uint16_t* idx = (uint16_t*)(tlo + cap);
   uint16_t* tidx = idx + cap;
+  uint32_t* cnt = (uint32_t*)(tidx + cap);
 
   __shared__ uint32_t st_off[64], st_m[64];
   __shared__ int sp;
@@ -117,10 +175,9 @@ __global__ void __launch_bounds__(kSplitThreads)
   __shared__ unsigned long long found;
   const uint32_t tid = threadIdx.x;
 
-  for (uint32_t j = tid; j < size; j += kSplitThreads) {
-    lo[j] = slo[start + j];
-    idx[j] = (uint16_t)j;
-  }
+  // a2 (second half): the bucket in (hi, lo) order; tlo holds hi until the
+  // first split, which only needs lo
+  sort_bucket(sfp + start, size, B, sub_bits, cnt, lo, tlo, idx, err);
   if (tid == 0) {
     sp = 0;
     st_off[sp] = 0;
@@ -227,20 +284,23 @@ __global__ void __launch_bounds__(kSplitThreads)
   __syncthreads();
   for (uint32_t j = tid; j < size; j += kSplitThreads) {
     llo[start + j] = lo[j];
-    lhi[start + j] = shi[start + idx[j]];
+    lhi[start + j] = sfp[start + idx[j]].y;
   }
 }
 
-shk_status launch_split(Ctx& c, const uint64_t* slo, const uint64_t* shi, const uint32_t* K,
-                        uint64_t B, uint32_t n, uint32_t max_bucket, const uint32_t* code_base,
-                        const uint32_t* leaf_base, uint64_t* codes, uint8_t* code_k,
-                        LeafDesc* leaves, uint64_t* llo, uint64_t* lhi, uint32_t* err) {
+shk_status launch_split(Ctx& c, const ulonglong2* sfp, const uint32_t* K, uint64_t B, uint32_t n,
+                        uint32_t max_bucket, const uint32_t* code_base, const uint32_t* leaf_base,
+                        uint64_t* codes, uint8_t* code_k, LeafDesc* leaves, uint64_t* llo,
+                        uint64_t* lhi, uint32_t* err) {
   if (B == 0) return SHK_OK;
   const uint32_t cap = (max_bucket + 7) & ~7u;
-  const size_t smem = (size_t)cap * (8 + 8 + 2 + 2);
+  uint32_t sub_bits = 5;  // about one sub-bin per key, at least 32
+  while ((1u << sub_bits) < max_bucket) sub_bits++;
+  const size_t smem = (size_t)cap * (8 + 8 + 2 + 2) + ((size_t)4 << sub_bits);
   SHK_CUDA(cudaFuncSetAttribute(k_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_split<<<(unsigned)B, kSplitThreads, smem, c.stream>>>(slo, shi, K, n, cap, code_base, leaf_base,
-                                                          codes, code_k, leaves, llo, lhi, err);
+  k_split<<<(unsigned)B, kSplitThreads, smem, c.stream>>>(sfp, K, B, n, cap, sub_bits, code_base,
+                                                          leaf_base, codes, code_k, leaves, llo,
+                                                          lhi, err);
   c.launches++;
   SHK_CUDA(cudaGetLastError());
   return SHK_OK;

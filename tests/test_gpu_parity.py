@@ -109,6 +109,48 @@ def test_string_and_fp128_keys(pkg, orc):
     assert np.array_equal(r.cpu().numpy().view(np.uint64), orc.query(want, lo, hi))
 
 
+@pytest.mark.parametrize("N", [30000, 180000])
+def test_many_buckets(pkg, orc, N):
+    """b = n = 2: 15,000 buckets (packed 16-bit shared-memory histogram) and
+    90,000 buckets (global histogram); both radix passes."""
+    keys = inp.distinct_u64(N, 600 + N)
+    m = pkg.shk_build(_dev(keys), 2, 2)
+    want = orc.build_mphf(keys, n=2, b=2)
+    assert m.serialize() == want
+    ranks = m.query(_dev(keys)).cpu().numpy().view(np.uint64)
+    assert _bijective(ranks, N)
+
+
+def test_long_and_many_strings(pkg, orc):
+    """Strings of 8..160 bytes: many warps' bytes exceed the shared-memory
+    staging buffer and are hashed from global memory; 15,000 buckets."""
+    import torch
+
+    data, offs = inp.ascii_strings(30000, 41, 8, 160)
+    want = orc.build_mphf(kind=orc.KEYS_STR, str_data=data, str_offsets=offs, n=2, b=2)
+    dd = torch.from_numpy(data).cuda()
+    do = torch.from_numpy(offs.view(np.int64)).cuda()
+    m = pkg.shk_build(dd, 2, 2, kind=pkg.SHK_KEYS_STR, str_offsets=do)
+    assert m.serialize() == want
+    lo, hi = orc.fingerprints_str(data, offs)
+    r = m.query(dd, kind=pkg.SHK_KEYS_STR, str_offsets=do)
+    assert np.array_equal(r.cpu().numpy().view(np.uint64), orc.query(want, lo, hi))
+
+
+def test_oversized_bucket_is_rejected(pkg):
+    """40,000 fingerprints in one bucket of 20,000 (b = 2): the packed
+    histogram counter passes 2^15 and spills; the build reports the bucket
+    above 8192 keys."""
+    N = 40000
+    fp = np.zeros((N, 2), np.uint64)
+    fp[:, 0] = inp.distinct_u64(N, 77)
+    fp[:, 1] = np.arange(N, dtype=np.uint64)  # hi < 2^64 / B: all in bucket 0
+    with pytest.raises(pkg.ShkError) as e:
+        pkg.shk_build(_dev(fp.reshape(-1)), 2, 2, kind=pkg.SHK_KEYS_FP128)
+    assert e.value.status == pkg.SHK_EINVAL
+    assert "8192" in str(e.value)
+
+
 def test_empty_and_errors(pkg, orc):
     import torch
 
