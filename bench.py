@@ -485,14 +485,16 @@ def run_strings(args):
     doffs = torch.from_numpy(offs.view(np.int64)).cuda()
     leaf, mode = 64, (pkg.SHK_LEAF_ROTATION if args.leaf_mode == "rf" else pkg.SHK_LEAF_PLAIN)
     w = min(count, 1_000_000)
-    pkg.shk_build(ddata, leaf, BUCKET, kind=pkg.SHK_KEYS_STR, str_offsets=doffs[:w + 1], leaf_mode=mode).close()
+    eps = args.eps_num
+    pkg.shk_build(ddata, leaf, BUCKET, kind=pkg.SHK_KEYS_STR, str_offsets=doffs[:w + 1], leaf_mode=mode,
+                  eps_num=eps).close()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         e0.record(stream)
         m = pkg.shk_build(ddata, leaf, BUCKET, kind=pkg.SHK_KEYS_STR, str_offsets=doffs, leaf_mode=mode,
-                          profile=True)
+                          eps_num=eps, profile=True)
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -516,7 +518,7 @@ def run_strings(args):
             "higher_is_better": True, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "mphf_build_1e8_strings_leaf64_bucket2000", "keys": count,
                        "string_bytes": int(data.size), "leaf_size": leaf, "bucket_size": BUCKET,
-                       "leaf_mode": args.leaf_mode},
+                       "leaf_mode": args.leaf_mode, "eps_num": eps or "default"},
             "bits_per_key": 8 * len(blob) / count, "bijection": bij, "query_s_all_keys": query_s,
             "phase_ms": {k: st[k] for k in ("ms_fingerprint", "ms_partition", "ms_split", "ms_leaf",
                                             "ms_orient", "ms_encode", "ms_ribbon", "ms_total")},
@@ -543,6 +545,9 @@ def main():
     ap.add_argument("--compare-per-bucket", action="store_true",
                     help="time the one-launch-per-bucket form on the whole workload (slow)")
     ap.add_argument("--requests", type=int, default=100, help="serve: number of requests")
+    ap.add_argument("--eps-num", type=int, default=983,
+                    help="strings: retrieval overhead eps = eps_num / 65536 (default 983, ~1.5 %%, "
+                         "for ~1.54 bits/key; 0: the library default, 3277)")
     ap.add_argument("--leafbatch-rf", dest="workload_leafbatch_rf", action="store_true",
                     help="leafbatch: rotation fitting (shk_leaf_search_rf)")
     ap.add_argument("--leaf-mode", default="rf", choices=["rf", "plain"],

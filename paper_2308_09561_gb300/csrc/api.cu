@@ -5,6 +5,9 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -61,6 +64,37 @@ struct PhaseTimer {
   }
 };
 
+
+shk_status blocks_per_sm(const void* kernel, int threads, size_t smem, int* out) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+  int dev = 0;
+  SHK_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_tuple(dev, kernel, threads, smem);
+  auto it = cache.find(key);
+  if (it == cache.end()) {
+    int n = 0;
+    SHK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem));
+    it = cache.emplace(key, n).first;
+  }
+  *out = it->second;
+  return SHK_OK;
+}
+
+shk_status raise_smem_limit(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  SHK_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[{dev, kernel}];
+  if (bytes > cur) {
+    SHK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+  }
+  return SHK_OK;
+}
 
 __global__ void k_u64_to_u32(const uint64_t* in, uint64_t n, uint32_t* out) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;

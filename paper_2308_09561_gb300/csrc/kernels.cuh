@@ -92,6 +92,15 @@ shk_status launch_ef_write_u64(Ctx& c, const uint64_t* v, uint64_t count, uint32
                                uint64_t* low, uint64_t* high);
 shk_status launch_ef_decode(Ctx& c, const uint64_t* low, const uint64_t* high, uint64_t hbits,
                             uint32_t l, uint64_t count, uint64_t* out);
+// Raise the dynamic shared memory limit of a kernel on the current device to
+// at least `bytes`.  The limit only ever grows (under a lock), so builds
+// running concurrently on several host threads never lower the limit that
+// another thread's launch relies on.
+shk_status raise_smem_limit(const void* kernel, size_t bytes);
+
+// Resident blocks per SM of a kernel for a launch shape (cached per device).
+shk_status blocks_per_sm(const void* kernel, int threads, size_t smem, int* out);
+
 shk_status launch_validate_index(Ctx& c, const uint32_t* K, const uint64_t* O, uint64_t B,
                                  uint64_t N, uint64_t rice_bits, uint32_t* bad);
 // a8

@@ -364,8 +364,7 @@ LeafCfg leaf_cfg_at(int i) { return kLeafTable[i].cfg; }
 
 static shk_status persistent_blocks(Ctx& c, const LeafKernels* k, uint32_t* blocks) {
   int per_sm = 0;
-  SHK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->persistent,
-                                                         (int)k->cfg.warps * 32, 0));
+  SHK_TRY(blocks_per_sm((const void*)k->persistent, (int)k->cfg.warps * 32, 0, &per_sm));
   if (per_sm < 1) per_sm = 1;
   *blocks = (uint32_t)(c.num_sms * per_sm);
   return SHK_OK;

@@ -513,8 +513,7 @@ shk_status launch_leaf_rf_persistent(Ctx& c, const LeafSearchArgs& a) {
   uint32_t* state;
   SHK_TRY(c.arena.alloc(&state, (size_t)L + nwords + 1, true));
   int per_sm = 0;
-  SHK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_rf_persistent,
-                                                         kRfWarps * 32, 0));
+  SHK_TRY(blocks_per_sm((const void*)k_leaf_rf_persistent, kRfWarps * 32, 0, &per_sm));
   if (per_sm < 1) per_sm = 1;
   const uint32_t blocks = (uint32_t)(c.num_sms * per_sm);
   k_leaf_rf_persistent<<<blocks, kRfWarps * 32, 0, c.stream>>>(

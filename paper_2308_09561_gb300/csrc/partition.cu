@@ -435,7 +435,7 @@ template <class Kern>
 static shk_status grid_for(Ctx& c, Kern k, int threads, size_t smem, uint64_t work_blocks,
                            int* blocks) {
   int per_sm = 0;
-  SHK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
+  SHK_TRY(blocks_per_sm((const void*)k, threads, smem, &per_sm));
   if (per_sm < 1) return fail(SHK_ECUDA, "fingerprint kernel does not fit on an SM");
   const uint64_t cap = (uint64_t)c.num_sms * per_sm;
   *blocks = (int)(work_blocks < cap ? (work_blocks ? work_blocks : 1) : cap);
@@ -452,15 +452,13 @@ shk_status launch_fingerprint(Ctx& c, int kind, const void* data, const uint64_t
     // one large block per SM when every block holds a large histogram
     const int threads = mode == 2 ? kStrThreadsMax : 256;
     const size_t smem = ((hbytes + 15) & ~(size_t)15) + (size_t)(threads / 32) * kStrBuf;
-    SHK_CUDA(cudaFuncSetAttribute(k_fingerprint_str, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    SHK_TRY(raise_smem_limit((const void*)k_fingerprint_str, smem));
     SHK_TRY(grid_for(c, k_fingerprint_str, threads, smem, (n_keys + threads - 1) / threads, &blocks));
     k_fingerprint_str<<<blocks, threads, smem, c.stream>>>((const uint8_t*)data, offs, n_keys, B, fp,
                                                            nullptr, nullptr, counts, mode);
   } else {
     const int threads = 512;
-    SHK_CUDA(cudaFuncSetAttribute(k_fingerprint, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)hbytes));
+    SHK_TRY(raise_smem_limit((const void*)k_fingerprint, hbytes));
     SHK_TRY(grid_for(c, k_fingerprint, threads, hbytes, (n_keys + threads - 1) / threads, &blocks));
     k_fingerprint<<<blocks, threads, hbytes, c.stream>>>(kind, data, offs, n_keys, B, fp, counts,
                                                          mode);
@@ -477,8 +475,7 @@ shk_status launch_fingerprint_only(Ctx& c, int kind, const void* data, const uin
   if (kind == SHK_KEYS_STR) {
     const int threads = 256;
     const size_t smem = (size_t)(threads / 32) * kStrBuf;
-    SHK_CUDA(cudaFuncSetAttribute(k_fingerprint_str, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    SHK_TRY(raise_smem_limit((const void*)k_fingerprint_str, smem));
     SHK_TRY(grid_for(c, k_fingerprint_str, threads, smem, (n_keys + threads - 1) / threads, &blocks));
     k_fingerprint_str<<<blocks, threads, smem, c.stream>>>((const uint8_t*)data, offs, n_keys, 1,
                                                            nullptr, lo, hi, nullptr, 0);
@@ -498,7 +495,7 @@ shk_status launch_scatter(Ctx& c, const ulonglong2* fp, uint32_t n_keys, uint64_
   while ((1ull << bbits) < B) bbits++;
   const uint32_t tiles = (n_keys + kRadixTile - 1) / kRadixTile;
   int per_sm = 0;
-  SHK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radix_pass, kRadixThreads, 0));
+  SHK_TRY(blocks_per_sm((const void*)k_radix_pass, kRadixThreads, 0, &per_sm));
   if (per_sm < 1) per_sm = 1;
   const uint32_t cap = (uint32_t)(c.num_sms * per_sm);
   const uint32_t grid = tiles < cap ? tiles : cap;

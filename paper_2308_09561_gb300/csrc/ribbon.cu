@@ -49,6 +49,31 @@ __device__ __forceinline__ int eliminate(uint64_t* rows, uint8_t* rhs, uint32_t*
   }
 }
 
+// Eliminates the rows plist[t0 .. t1) one after the other; a row that
+// reaches slot `limit` has its state written back and is passed to park(i).
+// Returns 0 if a row vanished with right-hand side 1.
+template <class Park>
+__device__ __forceinline__ int eliminate_list(uint64_t* rows, uint8_t* rhs, uint64_t* pcoef,
+                                              uint32_t* pstart, uint8_t* pbit,
+                                              const uint16_t* plist, uint32_t t0, uint32_t t1,
+                                              uint32_t limit, Park park) {
+  for (uint32_t t = t0; t < t1; t++) {
+    const uint32_t i = plist[t];
+    uint32_t st = pstart[i];
+    uint64_t cf = pcoef[i];
+    uint8_t bv = pbit[i];
+    const int res = eliminate(rows, rhs, &st, &cf, &bv, limit);
+    if (res == 0) return 0;
+    if (res == 2) {
+      pstart[i] = st;
+      pcoef[i] = cf;
+      pbit[i] = bv;
+      park(i);
+    }
+  }
+  return 1;
+}
+
 __global__ void k_shard_slots(const uint32_t* K, uint64_t B, uint32_t S, uint32_t eps_num,
                               uint64_t num_shards, uint64_t* slots) {
   const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,9 +111,10 @@ shk_status launch_max_shard_keys(Ctx& c, const uint32_t* K, uint64_t B, uint32_t
 }
 
 // Shared memory of one shard with row precomputation: rows[m] u64 |
-// coefficients[keys] u64 | starts[keys] u32 | rhs[m] u8 | bits[keys] u8.
+// coefficients[keys] u64 | starts[keys] u32 | region lists[keys] u16 |
+// rhs[m] u8 | bits[keys] u8.
 __host__ __device__ inline size_t ribbon_smem(uint64_t m, uint64_t keys, bool pre) {
-  return pre ? (size_t)m * 9 + (size_t)keys * 13 + 16 : (size_t)m * 9 + 16;
+  return pre ? (size_t)m * 9 + (size_t)keys * 15 + 32 : (size_t)m * 9 + 16;
 }
 
 template <bool PRE>
@@ -108,73 +134,108 @@ __global__ void __launch_bounds__(kRibbonThreads)
   }
   uint64_t* pcoef = rows + m;
   uint32_t* pstart = (uint32_t*)(pcoef + (PRE ? keys : 0));
-  uint8_t* rhs = PRE ? (uint8_t*)(pstart + keys) : (uint8_t*)(rows + m);
+  uint16_t* plist = (uint16_t*)(pstart + (PRE ? keys : 0));
+  uint8_t* rhs = PRE ? (uint8_t*)(plist + keys) : (uint8_t*)(rows + m);
   uint8_t* pbit = rhs + m;
   __shared__ int ok_s;
   __shared__ uint32_t seed_s;
+  __shared__ uint32_t rbase[kRegions + 1], rfill[kRegions], rpark[kRegions];
+  const uint32_t w = (uint32_t)((m + kRegions - 1) / kRegions);  // region width in slots
   for (uint32_t r = 0; r < kRibbonSeeds; r++) {
     for (uint64_t i = threadIdx.x; i < m; i += kRibbonThreads) {
       rows[i] = 0;
       rhs[i] = 0;
     }
-    if (PRE) {
-      for (uint32_t i = threadIdx.x; i < keys; i += kRibbonThreads) {
-        uint64_t st, cf;
-        ribbon_row(lo[k0 + i], hi[k0 + i], r, m, &st, &cf);
-        pcoef[i] = cf;
-        pstart[i] = (uint32_t)st;
-        pbit[i] = f[k0 + i];
-      }
-    }
+    if (threadIdx.x < kRegions) rfill[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
       ok_s = 1;
       seed_s = r;
     }
     __syncthreads();
     if (PRE) {
-      // Phase 1: lane 0 of every warp eliminates, in parallel with the other
-      // warps, the rows that start in its own slot range; a row that would
-      // step past its range is parked: bit 1 of its pbit is set, its start and
-      // coefficient stay as they were (other warps read them), and phase 2
-      // reduces it again from the start.  No slot and no row is written by
-      // two warps.
-      if ((threadIdx.x & 31) == 0) {
-        const uint32_t reg = threadIdx.x >> 5;
-        const uint32_t w = (uint32_t)((m + kRegions - 1) / kRegions);
-        const uint32_t r0 = reg * w, r1 = r0 + w < m ? r0 + w : (uint32_t)m;
-        int ok = 1;
-        for (uint32_t i = 0; i < keys && ok; i++) {
-          uint32_t st = pstart[i];
-          if (st < r0 || st >= r1) continue;
-          uint64_t cf = pcoef[i];
-          uint8_t bv = pbit[i];
-          const int res = eliminate(rows, rhs, &st, &cf, &bv, r1);
-          if (res == 0) ok = 0;
-          if (res == 2) pbit[i] |= 2;
+      // rows of this seed, listed by the region of their start slot
+      for (uint32_t i = threadIdx.x; i < keys; i += kRibbonThreads) {
+        uint64_t st, cf;
+        ribbon_row(lo[k0 + i], hi[k0 + i], r, m, &st, &cf);
+        pcoef[i] = cf;
+        pstart[i] = (uint32_t)st;
+        pbit[i] = f[k0 + i];
+        atomicAdd(&rfill[(uint32_t)st / w], 1u);
+      }
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        // exclusive scan of the kRegions (= 32) counts by one warp
+        const uint32_t lane = threadIdx.x, c = rfill[lane];
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+          if (lane >= (uint32_t)o) x += y;
         }
+        rbase[lane] = x - c;
+        if (lane == 31) rbase[kRegions] = x;
+        rfill[lane] = x - c;
+      }
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < keys; i += kRibbonThreads)
+        plist[atomicAdd(&rfill[pstart[i] / w], 1u)] = (uint16_t)i;
+      __syncthreads();
+      // Phase 1: lane 0 of warp g eliminates the rows that start in region g,
+      // slots [g w, (g + 1) w), in parallel with the other warps.  A row that
+      // would step past the region is parked: its partly reduced state is
+      // written back (only this lane owns the row) and its index is kept at
+      // the front of the region's list.
+      if ((threadIdx.x & 31) == 0) {
+        const uint32_t g = threadIdx.x >> 5;
+        const uint32_t r1 = (g + 1) * w < m ? (g + 1) * w : (uint32_t)m;
+        const uint32_t t0 = rbase[g], t1 = rbase[g + 1];
+        uint32_t np = t0;
+        const int ok = eliminate_list(rows, rhs, pcoef, pstart, pbit, plist, t0, t1, r1,
+                                      [&](uint32_t i) { plist[np++] = (uint16_t)i; });
+        rpark[g] = np - t0;
         if (!ok) ok_s = 0;
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0 && ok_s) {
-      // Phase 2 (or the whole elimination without row precomputation): one
-      // thread over the whole table.
+    if (PRE) {
+      // Phase 2: the rows parked at the end of region g continue in rounds;
+      // in round t they walk through region g + 1 + t (and are parked again
+      // at its end).  In a round every region works on a different region's
+      // slots, so all lanes run at once, and a row never leaves its region's
+      // list.  After a bounded number of rounds thread 0 finishes whatever is
+      // still waiting.
+      const uint32_t g = threadIdx.x >> 5;
+      const bool leader = (threadIdx.x & 31) == 0;
+      int pending = __syncthreads_or(leader && rpark[g] != 0);
+      uint32_t round = 0;
+      for (; pending && ok_s && round < kRegions; round++) {
+        if (leader && rpark[g] != 0) {
+          const uint32_t end = g + 2 + round;
+          const uint32_t lim = end < kRegions ? end * w : 0xFFFFFFFFu;
+          uint32_t keep = 0;
+          const int ok = eliminate_list(
+              rows, rhs, pcoef, pstart, pbit, plist, rbase[g], rbase[g] + rpark[g], lim,
+              [&](uint32_t i) { plist[rbase[g] + keep++] = (uint16_t)i; });
+          rpark[g] = keep;
+          if (!ok) ok_s = 0;
+        }
+        pending = __syncthreads_or(leader && rpark[g] != 0);
+      }
+      if (threadIdx.x == 0 && ok_s && pending) {
+        int ok = 1;
+        for (uint32_t h = 0; h < kRegions && ok; h++)
+          ok = eliminate_list(rows, rhs, pcoef, pstart, pbit, plist, rbase[h], rbase[h] + rpark[h],
+                                 0xFFFFFFFFu, [](uint32_t) {});
+        ok_s = ok;
+      }
+    } else if (threadIdx.x == 0) {
+      // without row precomputation: one thread over the whole table
       int ok = 1;
       for (uint32_t i = 0; i < keys && ok; i++) {
-        uint32_t st;
-        uint64_t cf;
-        uint8_t bv;
-        if (PRE) {
-          if (!(pbit[i] & 2)) continue;
-          st = pstart[i];
-          cf = pcoef[i];
-          bv = pbit[i] & 1;
-        } else {
-          uint64_t st64;
-          ribbon_row(lo[k0 + i], hi[k0 + i], r, m, &st64, &cf);
-          st = (uint32_t)st64;
-          bv = f[k0 + i];
-        }
+        uint64_t st64, cf;
+        ribbon_row(lo[k0 + i], hi[k0 + i], r, m, &st64, &cf);
+        uint32_t st = (uint32_t)st64;
+        uint8_t bv = f[k0 + i];
         if (eliminate(rows, rhs, &st, &cf, &bv, 0xFFFFFFFFu) == 0) ok = 0;
       }
       ok_s = ok;
@@ -187,25 +248,91 @@ __global__ void __launch_bounds__(kRibbonThreads)
     if (threadIdx.x == 0) atomicOr(err, kErrRibbon);
     return;
   }
-  if (threadIdx.x == 0) {
-    seeds[sh] = (uint8_t)seed_s;
-    // back substitution from the top; window bit j-1 = solution at i + j
-    uint64_t win = 0;
-    for (uint64_t i = m; i-- > 0;) {
-      const uint64_t row = rows[i];
-      uint8_t v = 0;
-      if (row) v = (uint8_t)((rhs[i] ^ __popcll((row >> 1) & win)) & 1);
-      rhs[i] = v;
-      win = (win << 1) | v;
+  if (threadIdx.x == 0) seeds[sh] = (uint8_t)seed_s;
+  // Back substitution from the top.  x[i] = rhs[i] + sum of x[i + j] over
+  // the set bits j of row i (pivot slots; 0 elsewhere).  With the column
+  // masks cm[p] (bit j = bit j of row p - j: the slots below p whose row
+  // holds x[p]) the serial step needs no popcount: acc bit t collects the
+  // sum for slot i - t, x[i] = rhs[i] + (acc bit 0), then acc ^= x[i] cm[i]
+  // and acc >>= 1.  cm and the packed pivot and rhs bits are built by all
+  // threads in the key-row arrays, which the elimination no longer needs;
+  // a shard too small for that (or without precomputed rows) takes the
+  // popcount form.  A finished 64-slot word of solution bits is kept in the
+  // first row slot of its range, which is no longer read.
+  const uint64_t nw = (m + 63) / 64;
+  const bool colmask = PRE && (size_t)keys * 14 >= (size_t)(m + 2 * nw) * 8;
+  if (colmask) {
+    uint64_t* cm = pcoef;
+    uint64_t* piv = cm + m;
+    uint64_t* rb = piv + nw;
+    for (uint64_t p = threadIdx.x; p < m; p += kRibbonThreads) {
+      uint64_t c = 0;
+      const uint32_t jmax = p < 63 ? (uint32_t)p : 63u;
+      for (uint32_t j = 1; j <= jmax; j++) c |= ((rows[p - j] >> j) & 1ull) << j;
+      cm[p] = c;
+    }
+    for (uint64_t w = threadIdx.x; w < nw; w += kRibbonThreads) {
+      uint64_t pv = 0, rv = 0;
+      for (uint32_t b = 0; b < 64 && w * 64 + b < m; b++) {
+        pv |= (uint64_t)(rows[w * 64 + b] != 0) << b;
+        rv |= (uint64_t)(rhs[w * 64 + b] & 1u) << b;
+      }
+      piv[w] = pv;
+      rb[w] = rv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t acc = 0;
+      for (int64_t w = (int64_t)nw - 1; w >= 0; w--) {
+        const uint64_t pv = piv[w], rv = rb[w];
+        const uint64_t* c = cm + (uint64_t)w * 64;
+        uint64_t out = 0;
+        const int top = (int)(m - 1 - (uint64_t)w * 64 < 63 ? m - 1 - (uint64_t)w * 64 : 63);
+        if (top == 63) {
+#pragma unroll 16
+          for (int b = 63; b >= 0; b--) {
+            const uint64_t v = (pv >> b) & ((rv >> b) ^ acc) & 1ull;
+            acc = (acc ^ (c[b] & (0ull - v))) >> 1;
+            out |= v << b;
+          }
+        } else {
+          for (int b = top; b >= 0; b--) {
+            const uint64_t v = (pv >> b) & ((rv >> b) ^ acc) & 1ull;
+            acc = (acc ^ (c[b] & (0ull - v))) >> 1;
+            out |= v << b;
+          }
+        }
+        rows[(uint64_t)w * 64] = out;
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    uint64_t win = 0, word = 0;  // win bit t = solution at slot i + 1 + t
+    for (int64_t grp = (int64_t)((m - 1) >> 3); grp >= 0; grp--) {
+      const uint64_t base = (uint64_t)grp * 8;
+      uint64_t rw[8];
+      uint32_t rv[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        rw[k] = base + k < m ? rows[base + k] : 0;
+        rv[k] = base + k < m ? rhs[base + k] : 0;
+      }
+#pragma unroll
+      for (int k = 7; k >= 0; k--) {
+        const uint64_t v = rw[k] ? (uint64_t)((rv[k] ^ __popcll((rw[k] >> 1) & win)) & 1u) : 0ull;
+        win = (win << 1) | v;
+        word |= v << ((base + k) & 63);
+      }
+      if ((base & 63) == 0) {
+        rows[base] = word;
+        word = 0;
+      }
     }
   }
   __syncthreads();
-  // pack the solution bits and OR them into the global vector
+  // OR the solution words into the global vector at the shard's bit offset
   const uint64_t base = shard_off[sh];
   for (uint64_t w = threadIdx.x; w * 64 < m; w += kRibbonThreads) {
-    uint64_t word = 0;
-    const uint64_t lim = m - w * 64 < 64 ? m - w * 64 : 64;
-    for (uint64_t j = 0; j < lim; j++) word |= (uint64_t)rhs[w * 64 + j] << j;
+    const uint64_t word = rows[w * 64];
     if (word == 0) continue;
     const uint64_t p = base + w * 64;
     const uint32_t s = (uint32_t)(p & 63);
@@ -226,12 +353,12 @@ shk_status launch_ribbon(Ctx& c, const uint64_t* lo, const uint64_t* hi, const u
   const size_t smem_pre = ribbon_smem(max_shard_slots, max_shard_slots, true);
   const size_t smem = ribbon_smem(max_shard_slots, 0, false);
   if (smem_pre <= limit) {
-    SHK_CUDA(cudaFuncSetAttribute(k_ribbon<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pre));
+    SHK_TRY(raise_smem_limit((const void*)k_ribbon<true>, smem_pre));
     k_ribbon<true><<<(unsigned)num_shards, kRibbonThreads, smem_pre, c.stream>>>(
         lo, hi, f, K, B, S, eps_num, shard_off, sol_words, seeds, err);
   } else {
     if (smem > limit) return fail(SHK_EINVAL, "retrieval shard too large for shared memory");
-    SHK_CUDA(cudaFuncSetAttribute(k_ribbon<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SHK_TRY(raise_smem_limit((const void*)k_ribbon<false>, smem));
     k_ribbon<false><<<(unsigned)num_shards, kRibbonThreads, smem, c.stream>>>(
         lo, hi, f, K, B, S, eps_num, shard_off, sol_words, seeds, err);
   }

@@ -297,7 +297,7 @@ shk_status launch_split(Ctx& c, const ulonglong2* sfp, const uint32_t* K, uint64
   uint32_t sub_bits = 5;  // about one sub-bin per key, at least 32
   while ((1u << sub_bits) < max_bucket) sub_bits++;
   const size_t smem = (size_t)cap * (8 + 8 + 2 + 2) + ((size_t)4 << sub_bits);
-  SHK_CUDA(cudaFuncSetAttribute(k_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SHK_TRY(raise_smem_limit((const void*)k_split, smem));
   k_split<<<(unsigned)B, kSplitThreads, smem, c.stream>>>(sfp, K, B, n, cap, sub_bits, code_base,
                                                           leaf_base, codes, code_k, leaves, llo,
                                                           lhi, err);

@@ -93,3 +93,25 @@ def test_a_failing_request_does_not_disturb_the_others(pkg):
             pkg.shk_server_poll(srv, r_host)  # already collected
     finally:
         pkg.shk_server_destroy(srv)
+
+
+def test_concurrent_builds_with_different_shared_memory_needs(pkg):
+    """Builds whose kernels need different dynamic shared memory (bucket
+    counts from 5 to 4000, bucket sizes 50 to 4096) run concurrently on 8
+    workers and each equals the same build alone."""
+    u = inp.uniform01(8, 64)
+    reqs = []
+    for i in range(32):
+        n_keys = int(2e4 * 10 ** u[2 * i])  # 2e4 .. 2e5
+        b = (50, 300, 1000, 4096)[int(u[2 * i + 1] * 4)]
+        reqs.append((inp.distinct_u64(n_keys, 20_000 + i), 16, b))
+    alone = [pkg.shk_build(k, n, b).serialize() for k, n, b in reqs]
+    srv = pkg.shk_server_create(0, 8)
+    try:
+        ids = [pkg.shk_server_submit(srv, k, n, b) for k, n, b in reqs]
+        for i, rid in enumerate(ids):
+            m, info = pkg.shk_server_wait(srv, rid)
+            assert info["status"] == 0
+            assert m.serialize() == alone[i]
+    finally:
+        pkg.shk_server_destroy(srv)
