@@ -32,6 +32,7 @@ METRIC = "MPHF build keys/s (1M u64 keys, leaf 48, bucket 2000), leaf seeds test
 # h1 adjust 2 (compare, add), two candidate bits into the mask: 8 when the mask
 # is two 32-bit words (2 subtracts, 4 shifts, 2 ors; m > 32), 3 for m <= 32
 OPS_PER_EVAL_WIDE = 14
+LEAF_TRAFFIC_PER_LEAF = 916_480 / 2_100  # DRAM bytes per leaf of the leaf kernel, measured with ncu
 OPS_PER_EVAL_NARROW = 9
 
 
@@ -287,7 +288,10 @@ def run_ours(args):
                       "ms_ribbon", "ms_total")},
         "roofline": {"bound": "alu", "kernel": "k_leaf_persistent", "achieved": achieved_tops,
                      "peak": peak_tops, "unit": "T int-lane-ops/s", "frac": achieved_tops / peak_tops,
-                     "traffic": None,
+                     # ncu dram read + write of k_leaf_persistent<4,8,4> on the 10^5-key build
+                     # (916.5 KB over 2,100 leaves), scaled by the leaves of this launch
+                     "traffic": LEAF_TRAFFIC_PER_LEAF * stats[-1]["n_leaves"],
+                     "traffic_note": "scaled by leaves from an ncu capture of the 10^5-key build",
                      "ops_per_launch": evals * OPS_PER_EVAL_WIDE,
                      "peak_note": f"{sms} SMs x 4 schedulers x 32 lanes x {sm_max_mhz:.0f} MHz (max SM clock)"},
         "e2e": {"value": e2e_value, "unit": "keys/s", "h2d_bytes_per_step": N_KEYS * 8,
