@@ -393,11 +393,12 @@ def run_leafbatch(args):
 
 def run_serve(args):
     """Served builds: a Poisson stream of MPHF build requests (uniform u64
-    keys, sizes log-uniform in [1e3, 3e5], leaf size 48 or 58 by coin, bucket
-    2000, stream seed 5, request i from sub-seed 5 + 7919 i) into one server
-    with 4 builds in flight.  The arrival rate is set for ~80 % offered load
-    from a calibration build of each leaf size.  Reports p50/p99 build latency
-    (submit to finish) and aggregate keys/s."""
+    keys, sizes log-uniform in [1e3, max_keys], leaf size 48 or 58 by coin,
+    bucket 2000, stream seed 5, request i from sub-seed 5 + 7919 i) into one
+    server with 4 builds in flight; plain or rotation-fitting leaves.  The
+    arrival rate is set for ~80 % offered load from a calibration build of
+    each leaf size.  Reports p50/p99 build latency (submit to finish) and
+    aggregate keys/s."""
     import torch
 
     import paper_2308_09561_gb300 as pkg
@@ -408,19 +409,22 @@ def run_serve(args):
     pkg.load_library()
     R = args.requests
     u = shk_inputs.uniform01(5 + 1000 * rank, 3 * R)
-    sizes = np.floor(10 ** (3 + np.log10(300) * u[0::3])).astype(np.int64)
+    sizes = np.floor(10 ** (3 + np.log10(args.max_keys / 1e3) * u[0::3])).astype(np.int64)
+    mode = pkg.SHK_LEAF_ROTATION if args.serve_rf else pkg.SHK_LEAF_PLAIN
     leafs = np.where(u[1::3] < 0.5, 48, 58)
-    reqs = [(shk_inputs.distinct_u64(int(sz), 5 + 7919 * i + 1000003 * rank), int(n))
+    # request keys are generated on the device (the same keys as distinct_u64)
+    reqs = [(shk_inputs.splitmix64_stream_torch(5 + 7919 * i + 1000003 * rank, int(sz), device="cuda"), int(n))
             for i, (sz, n) in enumerate(zip(sizes, leafs))]
+    torch.cuda.synchronize()
     # calibration: seconds per key of a build at each leaf size
     per_key = {}
     for n in (48, 58):
         k = shk_inputs.distinct_u64(60000, 77 + n)
-        pkg.shk_build(k, n, BUCKET).close()  # tuning / warm-up
+        pkg.shk_build(k, n, BUCKET, leaf_mode=mode).close()  # tuning / warm-up
         t = time.perf_counter()
-        pkg.shk_build(k, n, BUCKET).close()
+        pkg.shk_build(k, n, BUCKET, leaf_mode=mode).close()
         per_key[n] = (time.perf_counter() - t) / k.size
-    service = float(np.mean([k.size * per_key[n] for k, n in reqs]))
+    service = float(np.mean([k.numel() * per_key[n] for k, n in reqs]))
     rate = 0.8 / service
     gaps = -np.log(1.0 - shk_inputs.uniform01(55 + 1000 * rank, R)) / rate
     srv = pkg.shk_server_create(0, 4)
@@ -438,7 +442,7 @@ def run_serve(args):
                         if m is not None:
                             m.close()
                 time.sleep(0.0005)
-            pending[pkg.shk_server_submit(srv, keys, n, BUCKET)] = i
+            pending[pkg.shk_server_submit(srv, keys, n, BUCKET, leaf_mode=mode)] = i
         for rid in list(pending):
             m, info = pkg.shk_server_wait(srv, rid)
             infos.append(info)
@@ -449,12 +453,14 @@ def run_serve(args):
     lat = np.array([(i["finish_ns"] - i["submit_ns"]) / 1e6 for i in infos])
     ok = all(i["status"] == 0 for i in infos)
     span = (max(i["finish_ns"] for i in infos) - min(i["submit_ns"] for i in infos)) / 1e9
-    total = int(sum(k.size for k, _ in reqs))
+    total = int(sum(k.numel() for k, _ in reqs))
     line = {"metric": "served MPHF builds: aggregate keys/s, p50/p99 latency", "value": total / span,
             "unit": "keys/s", "n_gpus": ws, "steps": 1, "warmup": 2, "higher_is_better": True,
             "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "served_builds_poisson", "requests": R, "sizes": "log-uniform [1e3, 3e5]",
-                       "leaf_sizes": [48, 58], "bucket_size": BUCKET, "offered_load": 0.8, "workers": 4},
+            "config": {"workload": "served_builds_poisson", "requests": R,
+                       "sizes": f"log-uniform [1e3, {args.max_keys:.0e}]", "leaf_sizes": [48, 58],
+                       "leaf_mode": "rf" if args.serve_rf else "plain", "bucket_size": BUCKET,
+                       "offered_load": 0.8, "workers": 4},
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "all_ok": ok, "total_keys": total, "makespan_s": span,
             "arrival_rate_per_s": rate, "calibration_s_per_key": per_key,
@@ -549,6 +555,9 @@ def main():
     ap.add_argument("--compare-per-bucket", action="store_true",
                     help="time the one-launch-per-bucket form on the whole workload (slow)")
     ap.add_argument("--requests", type=int, default=100, help="serve: number of requests")
+    ap.add_argument("--max-keys", type=float, default=3e5,
+                    help="serve: largest request (sizes log-uniform from 1e3; 1e7 in the full stream)")
+    ap.add_argument("--serve-rf", action="store_true", help="serve: rotation-fitting leaves")
     ap.add_argument("--eps-num", type=int, default=983,
                     help="strings: retrieval overhead eps = eps_num / 65536 (default 983, ~1.5 %%, "
                          "for ~1.54 bits/key; 0: the library default, 3277)")

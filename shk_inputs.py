@@ -35,12 +35,33 @@ def splitmix64_stream(seed: int, count: int, start: int = 1) -> np.ndarray:
         return z ^ (z >> np.uint64(31))
 
 
+def _as_i64(x: int) -> int:
+    x &= 2**64 - 1
+    return x - 2**64 if x >= 2**63 else x
+
+
+def splitmix64_stream_torch(seed: int, count: int, start: int = 1, device="cuda"):
+    """The outputs of ``splitmix64_stream`` computed on ``device`` with torch
+    int64 arithmetic (wrapping multiply and add; logical right shifts by
+    masking); returns the 64-bit patterns as an int64 tensor."""
+    import torch
+
+    i = torch.arange(start, start + count, dtype=torch.int64, device=device)
+    z = i * _as_i64(int(_PHI)) + _as_i64(seed)
+    for sh, c in ((30, int(_C1)), (27, int(_C2))):
+        z = (z ^ ((z >> sh) & ((1 << (64 - sh)) - 1))) * _as_i64(c)
+    return z ^ ((z >> 31) & ((1 << 33) - 1))
+
+
 def uniform01(seed: int, count: int, start: int = 1) -> np.ndarray:
     return (splitmix64_stream(seed, count, start) >> np.uint64(11)).astype(np.float64) * (2.0**-53)
 
 
 def distinct_u64(count: int, seed: int) -> np.ndarray:
-    """First ``count`` distinct outputs of the stream, in stream order."""
+    """First ``count`` distinct outputs of the stream, in stream order.  The
+    output function is a bijection and the states are distinct, so these are
+    the first ``count`` outputs; ``splitmix64_stream_torch(seed, count)``
+    gives the same keys on a device."""
     out = np.empty(0, np.uint64)
     start = 1
     need = count
