@@ -78,6 +78,7 @@ def _load():
             "orc_orient": (i32, [vp, u32, u64, vp]),
             "orc_leaf_search_batch": (i32, [vp, vp, u32, u64, vp, vp, i32, i32]),
             "orc_bucket_build": (i32, [vp, vp, u32, u32, vp, vp, u32, vp, vp, i32]),
+            "orc_bucket_splits": (i32, [vp, vp, u32, u32, vp, vp, u32, vp, vp, vp, u32, vp]),
             "orc_rf_set": (i32, [u64]),
             "orc_rf_cells": (None, [u64, u64, u32, vp, vp]),
             "orc_rf_value": (i32, [vp, u32, u64, u64, i32, vp]),
@@ -277,6 +278,27 @@ def bucket_build(lo_sorted, hi_sorted, n: int, rf: bool = False):
     if st:
         raise OracleError(st, "bucket_build")
     return seeds[: nc.value].copy(), ks[: nc.value].copy(), lo, hi, f[:size].copy()
+
+
+def bucket_splits(lo_sorted, hi_sorted, n: int):
+    """One bucket's splitting tree without leaf searches: (codes in preorder,
+    all-ones in leaf slots; Rice parameters; lo, hi in leaf order; leaf
+    offsets; leaf sizes) for leaves of two or more keys."""
+    lo = _u64(lo_sorted).copy()
+    hi = _u64(hi_sorted).copy()
+    size = lo.size
+    cap = 2 * size + 8
+    seeds = np.zeros(cap, np.uint64)
+    ks = np.zeros(cap, np.uint8)
+    loff = np.zeros(max(size, 1), np.uint32)
+    lm = np.zeros(max(size, 1), np.uint32)
+    nc, nl = ctypes.c_uint32(), ctypes.c_uint32()
+    st = _load().orc_bucket_splits(_p(lo), _p(hi), size, n, _p(seeds), _p(ks), cap, ctypes.byref(nc),
+                                   _p(loff), _p(lm), loff.size, ctypes.byref(nl))
+    if st:
+        raise OracleError(st, "bucket_splits")
+    return (seeds[: nc.value].copy(), ks[: nc.value].copy(), lo, hi, loff[: nl.value].copy(),
+            lm[: nl.value].copy())
 
 
 def shard_slots(keys: int, eps_num: int = DEFAULT_EPS_NUM) -> int:

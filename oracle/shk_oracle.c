@@ -575,13 +575,29 @@ static int codes_push(codes_t* c, uint64_t seed, uint32_t k) {
   return 1;
 }
 
+/* Leaves of a bucket, recorded instead of searched (splits-only mode). */
+typedef struct {
+  uint32_t* off;
+  uint32_t* m;
+  uint32_t cap, n;
+} leafrec_t;
+
 static int build_node(uint64_t* lo, uint64_t* hi, uint8_t* f, uint32_t m, uint32_t n,
-                      codes_t* codes, uint64_t* tlo, uint64_t* thi, int rf) {
+                      codes_t* codes, uint64_t* tlo, uint64_t* thi, int rf, leafrec_t* lr,
+                      uint32_t base) {
   uint32_t unit, fan;
   if (!orc_split_shape(m, n, &unit, &fan)) {
     if (m == 1) {
       f[0] = 0;
       return ORC_OK;
+    }
+    if (lr) {
+      /* splits only: the leaf's code slot holds a marker, its keys stay put */
+      if (lr->n >= lr->cap) return ORC_EINVAL;
+      lr->off[lr->n] = base;
+      lr->m[lr->n] = m;
+      lr->n++;
+      return codes_push(codes, ~0ull, orc_rice_k_leaf(m)) ? ORC_OK : ORC_ENOMEM;
     }
     uint64_t s;
     int st = rf ? orc_rf_value(lo, m, 0, ORC_SEED_CAP, 1, &s)
@@ -608,7 +624,7 @@ static int build_node(uint64_t* lo, uint64_t* hi, uint8_t* f, uint32_t m, uint32
   uint32_t off = 0;
   for (uint32_t j = 0; j < fan; j++) {
     uint32_t p = part_size(m, unit, fan, j);
-    st = build_node(lo + off, hi + off, f + off, p, n, codes, tlo, thi, rf);
+    st = build_node(lo + off, hi + off, f + off, p, n, codes, tlo, thi, rf, lr, base + off);
     if (st != ORC_OK) return st;
     off += p;
   }
@@ -626,7 +642,7 @@ int orc_bucket_build(uint64_t* lo, uint64_t* hi, uint32_t size, uint32_t n, uint
   codes_t c = {0};
   uint64_t* tlo = (uint64_t*)malloc((size_t)size * 8);
   uint64_t* thi = (uint64_t*)malloc((size_t)size * 8);
-  int st = (tlo && thi) ? build_node(lo, hi, f, size, n, &c, tlo, thi, rf) : ORC_ENOMEM;
+  int st = (tlo && thi) ? build_node(lo, hi, f, size, n, &c, tlo, thi, rf, NULL, 0) : ORC_ENOMEM;
   if (st == ORC_OK) {
     if (c.n > cap) st = ORC_EINVAL;
     else {
@@ -635,6 +651,38 @@ int orc_bucket_build(uint64_t* lo, uint64_t* hi, uint32_t size, uint32_t n, uint
       *ncodes = c.n;
     }
   }
+  free(tlo);
+  free(thi);
+  free(c.seed);
+  free(c.k);
+  return st;
+}
+
+/* The splitting tree of one bucket without the leaf searches: codes in
+ * preorder with all-ones in the leaf slots, keys reordered into leaf order,
+ * and each leaf's (offset, size) for leaves of two or more keys, in order. */
+int orc_bucket_splits(uint64_t* lo, uint64_t* hi, uint32_t size, uint32_t n, uint64_t* seeds,
+                      uint8_t* ks, uint32_t cap, uint32_t* ncodes, uint32_t* leaf_off,
+                      uint32_t* leaf_m, uint32_t leaf_cap, uint32_t* nleaves) {
+  *ncodes = 0;
+  *nleaves = 0;
+  if (size == 0) return ORC_OK;
+  codes_t c = {0};
+  leafrec_t lr = {leaf_off, leaf_m, leaf_cap, 0};
+  uint8_t* f = (uint8_t*)malloc(size);
+  uint64_t* tlo = (uint64_t*)malloc((size_t)size * 8);
+  uint64_t* thi = (uint64_t*)malloc((size_t)size * 8);
+  int st = (f && tlo && thi) ? build_node(lo, hi, f, size, n, &c, tlo, thi, 0, &lr, 0) : ORC_ENOMEM;
+  if (st == ORC_OK) {
+    if (c.n > cap) st = ORC_EINVAL;
+    else {
+      memcpy(seeds, c.seed, (size_t)c.n * 8);
+      memcpy(ks, c.k, c.n);
+      *ncodes = c.n;
+      *nleaves = lr.n;
+    }
+  }
+  free(f);
   free(tlo);
   free(thi);
   free(c.seed);
@@ -873,7 +921,7 @@ int orc_build(int kind, const void* data, const uint64_t* offs, uint64_t N, uint
     uint64_t* tlo = (uint64_t*)malloc((size_t)size * 8);
     uint64_t* thi = (uint64_t*)malloc((size_t)size * 8);
     int st = (tlo && thi)
-                 ? build_node(lo + K[i], hi + K[i], f + K[i], size, n, &bc[i], tlo, thi, leaf_mode)
+                 ? build_node(lo + K[i], hi + K[i], f + K[i], size, n, &bc[i], tlo, thi, leaf_mode, NULL, 0)
                  : ORC_ENOMEM;
     free(tlo);
     free(thi);

@@ -370,6 +370,64 @@ def test_rotation_fitting_million_keys_sampled(pkg, orc):
     assert np.array_equal(orc.query(blob, lo[samp], hi[samp]), ranks.cpu().numpy().view(np.uint64)[samp])
 
 
+@pytest.mark.parametrize("eps", [983, 655])
+def test_retrieval_overhead_option(pkg, orc, eps):
+    """Builds at eps = 1.5 % and 1 % (shard seeds retried more often) equal
+    the oracle's bytes."""
+    keys = inp.distinct_u64(40000, 300 + eps)
+    for leaf_mode in (0, 1):
+        m = pkg.shk_build(_dev(keys), 16, 2000, eps_num=eps, leaf_mode=leaf_mode)
+        assert m.serialize() == orc.build_mphf(keys, n=16, b=2000, eps_num=eps, leaf_mode=leaf_mode)
+        m.close()
+
+
+def test_string_keys_leaf64_rotation_fitting_sampled(pkg, orc):
+    """The 10^8-string workload's parameters on 2 * 10^5 strings (lengths
+    10..50, bytes 1..127, stream seed 4): n = 64, b = 2000, rotation fitting,
+    eps = 1.5 %.  Every key ranks bijectively; bucket sizes, the split codes
+    of a sampled bucket, its smallest leaf and its full leaf with the
+    smallest value equal the oracle's; sampled ranks equal the oracle's
+    decoding of the GPU bytes."""
+    import torch
+
+    N, n, b = 200_000, 64, 2000
+    data, offs = inp.ascii_strings(N, 4)
+    dd = torch.from_numpy(data).cuda()
+    do = torch.from_numpy(offs.view(np.int64)).cuda()
+    m = pkg.shk_build(dd, n, b, kind=pkg.SHK_KEYS_STR, str_offsets=do, leaf_mode=pkg.SHK_LEAF_ROTATION,
+                      eps_num=983)
+    blob = m.serialize()
+    ranks = m.query(dd, kind=pkg.SHK_KEYS_STR, str_offsets=do)
+    srt, _ = torch.sort(ranks)
+    assert torch.equal(srt, torch.arange(N, device="cuda", dtype=torch.int64))
+    bl = Blob(blob)
+    assert bl.h["leaf_mode"] == 1 and bl.h["eps_num"] == 983
+    B = bl.h["B"]
+    K, O = bl.K(), bl.O()
+    lo, hi = orc.fingerprints_str(data, offs)
+    bkt = np.array((hi.astype(object) * B) >> 64, dtype=np.int64)
+    assert np.array_equal(np.bincount(bkt, minlength=B), np.diff(K.astype(np.int64)))
+    order = np.lexsort((lo, hi))
+    i = 37
+    sel = order[K[i]:K[i + 1]]
+    seeds, ks, llo, _, loff, lm = orc.bucket_splits(lo[sel], hi[sel], n)
+    codes, end = bl.rice_codes(int(O[i]), [int(k) for k in ks])
+    assert end == O[i + 1]
+    codes = np.array(codes, dtype=np.uint64)
+    leaf = seeds == np.uint64(2**64 - 1)
+    assert np.array_equal(codes[~leaf], seeds[~leaf])
+    gpu_leaf = codes[leaf]
+    short = int(np.argmin(lm))
+    full = [j for j in range(lm.size) if lm[j] == n and j != short]
+    pick = [short, min(full, key=lambda j: int(gpu_leaf[j]))]
+    packed = np.concatenate([llo[loff[j]:loff[j] + lm[j]] for j in pick])
+    po = np.array([0, lm[pick[0]], lm[pick[0]] + lm[pick[1]]], np.uint32)
+    assert np.array_equal(orc.leaf_search_batch(packed, po, 0, rf=True)[0], gpu_leaf[pick])
+    samp = np.arange(0, N, 53)
+    assert np.array_equal(orc.query(blob, lo[samp], hi[samp]), ranks.cpu().numpy().view(np.uint64)[samp])
+    m.close()
+
+
 @pytest.mark.parametrize("count,seed,lo_m,hi_m", [(2000, 81, 1, 40), (12, 82, 56, 64), (300, 83, 33, 48)])
 def test_rotation_fitting_leaf_search_equals_oracle(pkg, orc, count, seed, lo_m, hi_m):
     import torch

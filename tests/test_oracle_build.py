@@ -209,3 +209,22 @@ def test_leaves_made_by_splits_behave_like_random_leaves(orc):
     se = t.std() / math.sqrt(t.size)
     assert t.size > 12000
     assert abs(t.mean() - 33.04) < 5 * se + 0.2
+
+
+@pytest.mark.parametrize("n", [8, 24, 40])
+def test_splits_only_equals_the_full_bucket_build(orc, n):
+    """The splits-only bucket walk gives the full build's split codes, Rice
+    parameters and leaf order, and its leaves searched one by one give the
+    full build's leaf codes."""
+    keys = inp.distinct_u64(4000, 21)
+    lo, hi = orc.fingerprints_u64(keys)
+    o = np.lexsort((lo, hi))[:1500]
+    full = orc.bucket_build(lo[o], hi[o], n)
+    seeds, ks, llo, lhi, loff, lm = orc.bucket_splits(lo[o], hi[o], n)
+    leaf = seeds == np.uint64(2**64 - 1)
+    assert np.array_equal(ks, full[1]) and np.array_equal(llo, full[2]) and np.array_equal(lhi, full[3])
+    assert np.array_equal(seeds[~leaf], full[0][~leaf]) and int(leaf.sum()) == lm.size
+    offs = np.zeros(lm.size + 1, np.uint32)
+    offs[1:] = np.cumsum(lm)
+    packed = np.concatenate([llo[a:a + m] for a, m in zip(loff, lm)])
+    assert np.array_equal(orc.leaf_search_batch(packed, offs, 0)[0], full[0][leaf])
