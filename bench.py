@@ -266,6 +266,21 @@ def run_ours(args):
                 "leaf_candidates_per_s": rf_stats[-1]["leaf_seeds_min"] / (rf_stats[-1]["ms_leaf"] / 1e3),
                 "bits_per_key": 8 * rf_bytes / N_KEYS,
                 "note": "candidates = sum over leaves of (v+1), v = seed*m + rotation"}
+    # queries: every key of the workload, device in and out, L2 flushed before each pass
+    mq = pkg.shk_build(dkeys, LEAF, BUCKET)
+    mq.query(dkeys)
+    q_ms = []
+    for i in range(5):
+        flush.fill_(i)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mq.query(dkeys)
+        b.record(stream)
+        torch.cuda.synchronize()
+        q_ms.append(a.elapsed_time(b))
+    mq.close()
+    query = {"keys_per_s": N_KEYS / (float(np.median(q_ms)) / 1e3), "ms": float(np.median(q_ms)),
+             "note": "shk_query over all keys (fingerprint, bucket, Rice descent, retrieval parity)"}
     per_bucket = {"keys": cmp_keys, "persistent_ms_leaf": t_cmp["persistent"]["ms_leaf"],
                   "per_bucket_ms_leaf": t_cmp["per_bucket"]["ms_leaf"],
                   "per_bucket_leaf_launches": t_cmp["per_bucket"]["leaf_launches"],
@@ -300,6 +315,7 @@ def run_ours(args):
         "leaf_kernel_cfg": stats[-1]["leaf_cfg"],
         "persistent_vs_per_bucket": per_bucket,
         "rotation_fitting": rotation,
+        "query": query,
         "wall_s_timed": wall,
     }
     if clocks:

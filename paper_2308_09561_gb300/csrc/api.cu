@@ -719,9 +719,9 @@ extern "C" shk_status shk_leaf_tune(uint32_t leaf_size, uint32_t* cfg_out, doubl
   cfg_out[1] = cfg.warps;
   cfg_out[2] = cfg.unroll;
   cfg_out[3] = cfg.passes;
-  if (evals_per_s) SHK_TRY(probe_leaf_cfg(c, cfg, leaf_size, evals_per_s));
+  if (evals_per_s) SHK_TRY(probe_leaf_cfg(c, cfg, leaf_size, evals_per_s, 3));
   if (probe_all && all_evals_per_s)
-    for (int i = 0; i < leaf_cfg_count(); i++) SHK_TRY(probe_leaf_cfg(c, leaf_cfg_at(i), leaf_size, &all_evals_per_s[i]));
+    for (int i = 0; i < leaf_cfg_count(); i++) SHK_TRY(probe_leaf_cfg(c, leaf_cfg_at(i), leaf_size, &all_evals_per_s[i], 3));
   return SHK_OK;
 }
 

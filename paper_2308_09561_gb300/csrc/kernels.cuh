@@ -65,7 +65,7 @@ shk_status launch_leaf_persistent_state(Ctx& c, const LeafSearchArgs& a, uint32_
 shk_status launch_leaf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1);
 // autotuner: the fastest configuration for leaves of m keys on this device
 shk_status tuned_leaf_cfg(Ctx& c, uint32_t m, LeafCfg* out);
-shk_status probe_leaf_cfg(Ctx& c, const LeafCfg& cfg, uint32_t m, double* evals_per_s);
+shk_status probe_leaf_cfg(Ctx& c, const LeafCfg& cfg, uint32_t m, double* evals_per_s, int runs = 1);
 bool leaf_cfg_valid(const LeafCfg& c);
 int leaf_cfg_count();
 LeafCfg leaf_cfg_at(int i);
