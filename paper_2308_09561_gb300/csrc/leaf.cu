@@ -105,14 +105,14 @@ __device__ uint64_t search_seeds(WarpScratch* ws, uint32_t m, uint64_t s0, uint3
     const uint64_t base = s0 + (uint64_t)pass * (32u * U);
     if (best != nullptr && base >= read_uniform(best)) return ~0ull;
     *done += 32u * U;
-    uint32_t cl[U], ch[U], mlo[U], mhi[U];
+    uint32_t cl[U], ch[U];
+    uint64_t mask[U];  // covered cells; bit h = cell h (m <= 32: the low word only)
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const uint64_t c = mix64(kLeafSalt + base + (uint64_t)(u * 32) + lane);
       cl[u] = (uint32_t)c;
       ch[u] = (uint32_t)(c >> 32);
-      mlo[u] = 0;
-      mhi[u] = 0;
+      mask[u] = 0;
     }
 #pragma unroll UNROLL
     for (uint32_t i = 0; i < m; i++) {
@@ -126,15 +126,18 @@ __device__ uint64_t search_seeds(WarpScratch* ws, uint32_t m, uint64_t s0, uint3
         const uint32_t h0 = (uint32_t)(w >> 32);
         const uint32_t t = __umulhi((uint32_t)w, m1);
         const uint32_t h1 = t + (t >= h0 ? 1u : 0u);
-        mlo[u] |= bit32(h0) | bit32(h1);
-        if (WIDE) mhi[u] |= bit32(h0 - 32u) | bit32(h1 - 32u);
+        if (WIDE)
+          mask[u] |= (1ull << h0) | (1ull << h1);
+        else
+          mask[u] |= bit32(h0) | bit32(h1);
       }
     }
+    const uint64_t full = ((uint64_t)full_hi << 32) | full_lo;
     bool any = false;
     bool cov[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      cov[u] = mlo[u] == full_lo && (!WIDE || mhi[u] == full_hi);
+      cov[u] = mask[u] == full;
       any |= cov[u];
     }
     if (__ballot_sync(kFull, any)) {
@@ -304,22 +307,6 @@ __global__ void __launch_bounds__(WARPS * 32)
 
 // Throughput probe for the tuner: every warp searches fixed seed ranges of a
 // synthetic leaf of m keys and counts the seeds it evaluated.
-template <int U, int WARPS, int UNROLL>
-__global__ void __launch_bounds__(WARPS * 32)
-    k_leaf_probe(const uint64_t* __restrict__ keys, uint32_t m, uint32_t rounds,
-                 unsigned long long* executed) {
-  __shared__ WarpScratch scratch[WARPS];
-  const uint32_t lane = threadIdx.x & 31;
-  WarpScratch* ws = &scratch[threadIdx.x >> 5];
-  const uint32_t gw = blockIdx.x * WARPS + (threadIdx.x >> 5);
-  for (uint32_t i = lane; i < m; i += 32) ws->x[i] = leaf_input(keys[(uint64_t)gw * kMaxLeaf + i]);
-  __syncwarp();
-  uint32_t done = 0;
-  for (uint32_t r = 0; r < rounds; r++)
-    (void)search_dispatch<U, UNROLL>(ws, m, (uint64_t)r << 32, 4, nullptr, &done);
-  if (lane == 0) atomicAdd(executed, (unsigned long long)done);
-}
-
 __global__ void k_probe_keys(uint64_t* keys, uint64_t n, uint64_t salt) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) keys[i] = mix64(salt + i * 0x9E3779B97F4A7C15ull);
@@ -335,11 +322,9 @@ struct LeafKernels {
                      uint32_t*);
   void (*range)(const LeafDesc*, uint32_t, uint32_t, const uint64_t*, uint64_t, uint32_t,
                 unsigned long long*, unsigned long long*, uint32_t*);
-  void (*probe)(const uint64_t*, uint32_t, uint32_t, unsigned long long*);
 };
 
-#define SHK_LEAF_CFG(U, W, R) \
-  {{U, W, R, 0}, k_leaf_persistent<U, W, R>, k_leaf_range<U, W, R>, k_leaf_probe<U, W, R>}
+#define SHK_LEAF_CFG(U, W, R) {{U, W, R, 0}, k_leaf_persistent<U, W, R>, k_leaf_range<U, W, R>}
 
 static const LeafKernels kLeafTable[] = {
     SHK_LEAF_CFG(1, 8, 2), SHK_LEAF_CFG(2, 4, 2), SHK_LEAF_CFG(2, 8, 2), SHK_LEAF_CFG(2, 8, 4),
@@ -439,31 +424,52 @@ static TuneSlot g_tune[64][4];
 
 static uint32_t default_passes(uint32_t m) { return m <= 16 ? 2u : (m <= 32 ? 4u : 8u); }
 
+__global__ void k_probe_descs(LeafDesc* d, uint32_t n_leaves, uint32_t m) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_leaves) d[i] = LeafDesc{i * m, m, kNoCode, 0};
+}
+
+// Rate of a configuration: the persistent kernel itself (same code, registers,
+// occupancy and work sharing as in a build) on two synthetic leaves of m keys
+// per warp, at the passes per work item a build uses.  The search starts 4096
+// seeds below the seed cap, so each leaf ends at its solution or at the cap
+// (a runtime bound in the kernel instead would change its code: measured 7 %
+// slower at 4 seeds x 8 warps x unroll 4).  Key-seed evaluations per second
+// of the best of `runs` timed launches.
 shk_status probe_leaf_cfg(Ctx& c, const LeafCfg& cfg, uint32_t m, double* evals_per_s, int runs) {
   const LeafKernels* k = find_kernels(cfg);
   if (!k) return fail(SHK_EINVAL, "unsupported leaf kernel configuration");
+  if (m < 2 || m > kMaxLeaf) return fail(SHK_EINVAL, "leaf size must be in [2, 64]");
   uint32_t blocks;
   SHK_TRY(persistent_blocks(c, k, &blocks));
-  const uint64_t warps = (uint64_t)blocks * cfg.warps;
+  const uint32_t L = 2 * blocks * cfg.warps, nwords = (L + 31) / 32;
+  const uint32_t passes = default_passes(m);
   uint64_t* keys;
-  unsigned long long* cnt;
-  SHK_TRY(c.arena.alloc(&keys, warps * kMaxLeaf));
-  SHK_TRY(c.arena.alloc(&cnt, 1, true));
-  k_probe_keys<<<(unsigned)((warps * kMaxLeaf + 255) / 256), 256, 0, c.stream>>>(keys, warps * kMaxLeaf,
-                                                                                (uint64_t)m << 40);
-  c.launches++;
-  const uint32_t rounds = (uint32_t)std::max<uint64_t>(1, 64 / cfg.seeds_per_lane);
+  LeafDesc* descs;
+  unsigned long long *best, *cnt;
+  uint32_t *state, *err;
+  SHK_TRY(c.arena.alloc(&keys, (size_t)L * m));
+  SHK_TRY(c.arena.alloc(&descs, L));
+  SHK_TRY(c.arena.alloc(&best, L));
+  SHK_TRY(c.arena.alloc(&cnt, 1));
+  SHK_TRY(c.arena.alloc(&state, (size_t)L + nwords + 1));
+  SHK_TRY(c.arena.alloc(&err, 1));
+  k_probe_keys<<<(unsigned)(((uint64_t)L * m + 255) / 256), 256, 0, c.stream>>>(keys, (uint64_t)L * m,
+                                                                              (uint64_t)m << 40);
+  k_probe_descs<<<(L + 255) / 256, 256, 0, c.stream>>>(descs, L, m);
+  c.launches += 2;
   cudaEvent_t e0, e1;
   SHK_CUDA(cudaEventCreate(&e0));
   SHK_CUDA(cudaEventCreate(&e1));
-  k->probe<<<blocks, cfg.warps * 32, 0, c.stream>>>(keys, m, rounds / 4 + 1, cnt);  // warm-up
-  c.launches++;
-  // the rate of the best of `runs` timed launches
-  double best = 0;
-  for (int run = 0; run < runs; run++) {
+  double top = 0;
+  for (int run = -1; run < runs; run++) {  // run -1: warm-up
+    SHK_CUDA(cudaMemsetAsync(best, 0xFF, (size_t)L * 8, c.stream));
+    SHK_CUDA(cudaMemsetAsync(state, 0, ((size_t)L + nwords + 1) * 4, c.stream));
     SHK_CUDA(cudaMemsetAsync(cnt, 0, 8, c.stream));
     SHK_CUDA(cudaEventRecord(e0, c.stream));
-    k->probe<<<blocks, cfg.warps * 32, 0, c.stream>>>(keys, m, rounds, cnt);
+    k->persistent<<<blocks, cfg.warps * 32, 0, c.stream>>>(descs, L, keys, kSeedCap - 4096, passes,
+                                                          best, state, state + L, state + L + nwords,
+                                                          cnt, err);
     SHK_CUDA(cudaEventRecord(e1, c.stream));
     c.launches++;
     unsigned long long h = 0;
@@ -472,11 +478,11 @@ shk_status probe_leaf_cfg(Ctx& c, const LeafCfg& cfg, uint32_t m, double* evals_
     float ms = 0;
     SHK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     const double r = ms > 0 ? (double)h * m / (ms * 1e-3) : 0;
-    if (r > best) best = r;
+    if (run >= 0 && r > top) top = r;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  *evals_per_s = best;
+  *evals_per_s = top;
   return SHK_OK;
 }
 
