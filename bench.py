@@ -32,7 +32,7 @@ METRIC = "MPHF build keys/s (1M u64 keys, leaf 48, bucket 2000), leaf seeds test
 # h1 adjust 2 (compare, add), two candidate bits into the mask: 8 when the mask
 # is two 32-bit words (2 subtracts, 4 shifts, 2 ors; m > 32), 3 for m <= 32
 OPS_PER_EVAL_WIDE = 14
-LEAF_TRAFFIC_PER_LEAF = 916_480 / 2_100  # DRAM bytes per leaf of the leaf kernel, measured with ncu
+LEAF_TRAFFIC_PER_LEAF = 920_576 / 2_100  # DRAM bytes per leaf of the leaf kernel, measured with ncu
 OPS_PER_EVAL_NARROW = 9
 
 
@@ -191,8 +191,13 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # 256 MB > L2
     stream = torch.cuda.current_stream()
 
+    cfg = {}
+    if args.leaf_cfg:
+        u, w, r = (int(v) for v in args.leaf_cfg.split(","))
+        cfg = {"seeds_per_lane": u, "warps_per_block": w, "key_unroll": r, "chunk_passes": 8}
+
     def step(profile=True):
-        m = pkg.shk_build(dkeys, LEAF, BUCKET, profile=profile)
+        m = pkg.shk_build(dkeys, LEAF, BUCKET, profile=profile, **cfg)
         st = m.stats()
         m.close()
         return st
@@ -227,7 +232,7 @@ def run_ours(args):
     for i in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        m = pkg.shk_build(host_keys, LEAF, BUCKET)
+        m = pkg.shk_build(host_keys, LEAF, BUCKET, **cfg)
         blob = m.serialize()
         e2e_ms.append(1e3 * (time.perf_counter() - t))
         blob_bytes = len(blob)
@@ -249,7 +254,7 @@ def run_ours(args):
     ck = dkeys[:cmp_keys]
     t_cmp = {}
     for name, sched in (("persistent", pkg.SHK_SCHED_PERSISTENT), ("per_bucket", pkg.SHK_SCHED_PER_BUCKET)):
-        m = pkg.shk_build(ck, LEAF, BUCKET, sched=sched, profile=True)
+        m = pkg.shk_build(ck, LEAF, BUCKET, sched=sched, profile=True, **cfg)
         st = m.stats()
         t_cmp[name] = st
         m.close()
@@ -267,7 +272,7 @@ def run_ours(args):
                 "bits_per_key": 8 * rf_bytes / N_KEYS,
                 "note": "candidates = sum over leaves of (v+1), v = seed*m + rotation"}
     # queries: every key of the workload, device in and out, L2 flushed before each pass
-    mq = pkg.shk_build(dkeys, LEAF, BUCKET)
+    mq = pkg.shk_build(dkeys, LEAF, BUCKET, **cfg)
     mq.query(dkeys)
     q_ms = []
     for i in range(5):
@@ -304,7 +309,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "k_leaf_persistent", "achieved": achieved_tops,
                      "peak": peak_tops, "unit": "T int-lane-ops/s", "frac": achieved_tops / peak_tops,
                      # ncu dram read + write of k_leaf_persistent<4,8,4> on the 10^5-key build
-                     # (916.5 KB over 2,100 leaves), scaled by the leaves of this launch
+                     # (920.6 KB over 2,100 leaves), scaled by the leaves of this launch
                      "traffic": LEAF_TRAFFIC_PER_LEAF * stats[-1]["n_leaves"],
                      "traffic_note": "scaled by leaves from an ncu capture of the 10^5-key build",
                      "ops_per_launch": evals * OPS_PER_EVAL_WIDE,
@@ -570,6 +575,9 @@ def main():
                     help="key (leafbatch: leaf) count other than the workload's own, for profiling runs")
     ap.add_argument("--compare-per-bucket", action="store_true",
                     help="time the one-launch-per-bucket form on the whole workload (slow)")
+    ap.add_argument("--leaf-cfg", default="",
+                    help="build: fix the leaf kernel configuration 'U,W,R' (seeds per lane, warps per "
+                         "block, key unroll) instead of the autotuner's (for profiling runs)")
     ap.add_argument("--requests", type=int, default=100, help="serve: number of requests")
     ap.add_argument("--max-keys", type=float, default=3e5,
                     help="serve: largest request (sizes log-uniform from 1e3; 1e7 in the full stream)")
