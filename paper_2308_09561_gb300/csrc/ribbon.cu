@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kRibbonThreads)
         int ok = 1;
         for (uint32_t h = 0; h < kRegions && ok; h++)
           ok = eliminate_list(rows, rhs, pcoef, pstart, pbit, plist, rbase[h], rbase[h] + rpark[h],
-                                 0xFFFFFFFFu, [](uint32_t) {});
+                              0xFFFFFFFFu, [](uint32_t) {});
         ok_s = ok;
       }
     } else if (threadIdx.x == 0) {
