@@ -220,18 +220,56 @@ __global__ void __launch_bounds__(kSplitThreads)
     const uint32_t t1 = u, t2 = f > 2 ? 2 * u : 0xFFFFFFFFu, t3 = f > 3 ? 3 * u : 0xFFFFFFFFu;
     const uint32_t e1 = m - u, e2 = f > 2 ? m - 2 * u : 0, e3 = f > 3 ? m - 3 * u : 0;
     const uint64_t g = mix64(kSplitSalt + m);
+    // the node's keys as (xor input, multiplier) pairs for the search; tlo is
+    // free until the partition below
+    uint2* xk = (uint2*)tlo;
+    for (uint32_t j = tid; j < m; j += kSplitThreads) {
+      const uint64_t x = lo[off + j];
+      xk[j] = make_uint2((uint32_t)(x >> 32), (uint32_t)x | 1u);
+    }
+    __syncthreads();
+    // Four equal parts (m = 4u <= 256): the child floor(v / u) of
+    // v = floor(a m / 2^32) is floor(4 a / 2^32), and 8 times it is
+    // floor(32 a / 2^32) with the low 3 bits cleared; the counts are kept in
+    // the four bytes of one word (a byte overflows only when all 256 keys
+    // fall into one child, which never matches the expected counts).
+    const bool equal4 = f == 4 && m == 4 * u && m <= 256;
     bool capped = false;
     for (uint64_t base = 0;; base += kSplitThreads) {
       const uint64_t s = base + tid;
       const uint64_t d = mix64(g + s);
-      uint32_t c1 = 0, c2 = 0, c3 = 0;
-      for (uint32_t j = 0; j < m; j++) {
-        const uint32_t v = split_value(lo[off + j], d, m);
-        c1 += v >= t1;
-        c2 += v >= t2;
-        c3 += v >= t3;
+      const uint32_t dl = (uint32_t)d, dh = (uint32_t)(d >> 32);
+      bool hit;
+      if (equal4) {
+        uint32_t acc = 0;
+        for (uint32_t j = 0; j < m; j++) {
+          const uint32_t a = (xk[j].x ^ dl) * xk[j].y + dh;
+          acc += 1u << (__umulhi(a, 32u) & ~7u);
+        }
+        hit = acc == u * 0x01010101u;
+      } else if (f == 2) {
+        uint32_t c1 = 0;
+        for (uint32_t j = 0; j < m; j++) c1 += __umulhi((xk[j].x ^ dl) * xk[j].y + dh, m) >= t1;
+        hit = c1 == e1;
+      } else if (f == 3) {
+        uint32_t c1 = 0, c2 = 0;
+        for (uint32_t j = 0; j < m; j++) {
+          const uint32_t v = __umulhi((xk[j].x ^ dl) * xk[j].y + dh, m);
+          c1 += v >= t1;
+          c2 += v >= t2;
+        }
+        hit = c1 == e1 && c2 == e2;
+      } else {
+        uint32_t c1 = 0, c2 = 0, c3 = 0;
+        for (uint32_t j = 0; j < m; j++) {
+          const uint32_t v = __umulhi((xk[j].x ^ dl) * xk[j].y + dh, m);
+          c1 += v >= t1;
+          c2 += v >= t2;
+          c3 += v >= t3;
+        }
+        hit = c1 == e1 && c2 == e2 && c3 == e3;
       }
-      if (c1 == e1 && c2 == e2 && c3 == e3) atomicMin(&found, (unsigned long long)s);
+      if (hit) atomicMin(&found, (unsigned long long)s);
       __syncthreads();
       const unsigned long long fnd = found;
       __syncthreads();
