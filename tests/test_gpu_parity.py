@@ -370,6 +370,17 @@ def test_rotation_fitting_million_keys_sampled(pkg, orc):
     assert np.array_equal(orc.query(blob, lo[samp], hi[samp]), ranks.cpu().numpy().view(np.uint64)[samp])
 
 
+@pytest.mark.parametrize("S", [1, 8])
+def test_shard_size_option(pkg, orc, S):
+    """Shards of one bucket (2,000 keys) and of eight (about 16,000 keys: too
+    large for precomputed rows in shared memory, so the retrieval kernel
+    eliminates on one thread) equal the oracle's bytes."""
+    keys = inp.distinct_u64(50000, 400 + S)
+    m = pkg.shk_build(_dev(keys), 24, 2000, shard_buckets=S)
+    assert m.serialize() == orc.build_mphf(keys, n=24, b=2000, shard_buckets=S)
+    m.close()
+
+
 @pytest.mark.parametrize("eps", [983, 655])
 def test_retrieval_overhead_option(pkg, orc, eps):
     """Builds at eps = 1.5 % and 1 % (shard seeds retried more often) equal
