@@ -285,7 +285,8 @@ def run_ours(args):
         q_ms.append(a.elapsed_time(b))
     mq.close()
     query = {"keys_per_s": N_KEYS / (float(np.median(q_ms)) / 1e3), "ms": float(np.median(q_ms)),
-             "note": "shk_query over all keys (fingerprint, bucket, Rice descent, retrieval parity)"}
+             "note": "shk_query over all keys (fingerprint, bucket, tree descent through the query "
+                     "index built by the first query, retrieval parity)"}
     per_bucket = {"keys": cmp_keys, "persistent_ms_leaf": t_cmp["persistent"]["ms_leaf"],
                   "per_bucket_ms_leaf": t_cmp["per_bucket"]["ms_leaf"],
                   "per_bucket_leaf_launches": t_cmp["per_bucket"]["leaf_launches"],

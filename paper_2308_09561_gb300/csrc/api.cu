@@ -146,6 +146,8 @@ static void free_mphf(shk_mphf* m) {
   if (m->d_K) cudaFree(m->d_K);
   if (m->d_O) cudaFree(m->d_O);
   if (m->d_shard_off) cudaFree(m->d_shard_off);
+  if (m->d_qnode) cudaFree(m->d_qnode);
+  if (m->d_qbase) cudaFree(m->d_qbase);
   delete m;
 }
 
@@ -517,6 +519,46 @@ extern "C" shk_status shk_deserialize(const uint8_t* buf, size_t len, shk_mphf**
   return SHK_OK;
 }
 
+// The query index of m: built once, by the first query, on that query's stream
+// (a cache of decoded codes; the object stays logically unchanged).  Published
+// only after the build finished, so a concurrent query on another stream sees
+// either no index or a complete one.
+static shk_status ensure_qindex(Ctx& c, shk_mphf* m) {
+  std::lock_guard<std::mutex> lk(m->qmu);
+  const uint64_t B = m->hdr[4];
+  if (m->d_qnode || B == 0) return SHK_OK;
+  const uint32_t n = (uint32_t)m->hdr[2];
+  uint32_t *nleaf, *ncode, *nsplit, *maxb;
+  SHK_TRY(c.arena.alloc(&nleaf, B));
+  SHK_TRY(c.arena.alloc(&ncode, B));
+  SHK_TRY(c.arena.alloc(&nsplit, B));
+  SHK_TRY(c.arena.alloc(&maxb, 1, true));
+  SHK_TRY(launch_tree_count(c, m->d_K, B, n, nleaf, ncode, nsplit, maxb));
+  uint32_t* qbase = nullptr;
+  QNode* nodes = nullptr;
+  auto cleanup = [&](shk_status st) {
+    cudaStreamSynchronize(c.stream);
+    if (qbase) cudaFree(qbase);
+    if (nodes) cudaFree(nodes);
+    return st;
+  };
+  if (cudaMalloc(&qbase, (B + 1) * 4) != cudaSuccess) return cleanup(fail(SHK_ENOMEM, "query index"));
+  shk_status st = exclusive_scan<uint32_t, uint32_t>(c, ncode, B, qbase);
+  if (st != SHK_OK) return cleanup(st);
+  uint32_t total = 0;
+  st = d2h(c, &total, qbase + B);
+  if (st != SHK_OK || cudaStreamSynchronize(c.stream) != cudaSuccess)
+    return cleanup(st != SHK_OK ? st : fail(SHK_ECUDA, "query index"));
+  if (cudaMalloc(&nodes, (size_t)(total ? total : 1) * sizeof(QNode)) != cudaSuccess)
+    return cleanup(fail(SHK_ENOMEM, "query index"));
+  st = launch_qindex_build(c, m, qbase, nodes);
+  if (st != SHK_OK || cudaStreamSynchronize(c.stream) != cudaSuccess)
+    return cleanup(st != SHK_OK ? st : fail(SHK_ECUDA, "query index"));
+  m->d_qbase = qbase;
+  m->d_qnode = nodes;
+  return SHK_OK;
+}
+
 extern "C" shk_status shk_query(const shk_mphf* m, const shk_keys* keys, uint64_t* ranks_out,
                                 int out_on_device, void* cuda_stream) {
   if (!m || !ranks_out) return fail(SHK_EINVAL, "NULL argument");
@@ -535,6 +577,7 @@ extern "C" shk_status shk_query(const shk_mphf* m, const shk_keys* keys, uint64_
     SHK_TRY(c.arena.alloc(&hi, nq));
     if (!out_on_device) SHK_TRY(c.arena.alloc(&ranks, nq));
     SHK_TRY(launch_fingerprint_only(c, keys->kind, kdata, koffs, nq, lo, hi));
+    if (nq) SHK_TRY(ensure_qindex(c, const_cast<shk_mphf*>(m)));
     SHK_TRY(launch_query(c, m, lo, hi, nq, ranks));
     if (!out_on_device && nq)
       SHK_CUDA(cudaMemcpyAsync(ranks_out, ranks, nq * 8, cudaMemcpyDeviceToHost, st));

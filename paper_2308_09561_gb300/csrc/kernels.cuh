@@ -115,5 +115,7 @@ shk_status launch_max_shard_keys(Ctx& c, const uint32_t* K, uint64_t B, uint32_t
 // query
 shk_status launch_query(Ctx& c, const shk_mphf* m, const uint64_t* lo, const uint64_t* hi,
                         uint64_t n, uint64_t* ranks);
+// query index: records of every bucket's codes (qbase: each bucket's first record)
+shk_status launch_qindex_build(Ctx& c, const shk_mphf* m, const uint32_t* qbase, QNode* nodes);
 
 }  // namespace shk

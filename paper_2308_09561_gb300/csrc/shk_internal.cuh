@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 
 #include "../../include/shk.h"
@@ -242,6 +243,17 @@ struct Arena {
 
 // The MPHF object: the encoded words on the device plus decoded index arrays
 // used by queries (not part of the encoded bits).
+namespace shk {
+// Query index: one record per code in preorder -- the code's value and, for a
+// split node, the distance from its record to the first record of children
+// 1..3 (child 0 follows at +1).
+struct __align__(16) QNode {
+  uint64_t seed;
+  uint16_t child[3];
+  uint16_t pad;
+};
+}  // namespace shk
+
 struct shk_mphf {
   uint64_t hdr[shk::kHeaderWords];
   uint64_t words = 0;          // total u64 words of the encoded form
@@ -253,6 +265,10 @@ struct shk_mphf {
   uint32_t* d_K = nullptr;          // B + 1 key prefix sums
   uint64_t* d_O = nullptr;          // B + 1 Rice bit offsets
   uint64_t* d_shard_off = nullptr;  // num_shards + 1 slot offsets
+  // query index, built by the first query (not part of the encoded form)
+  shk::QNode* d_qnode = nullptr;  // one record per code
+  uint32_t* d_qbase = nullptr;    // B + 1: first record of each bucket
+  std::mutex qmu;
   shk_stats stats{};
   int device = 0;
 };

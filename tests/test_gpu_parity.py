@@ -448,3 +448,27 @@ def test_rotation_fitting_leaf_search_equals_oracle(pkg, orc, count, seed, lo_m,
     v, f = pkg.shk_leaf_search_rf(_dev(keys), torch.from_numpy(offs.view(np.int32)).cuda())
     assert np.array_equal(v.cpu().numpy().view(np.uint64), want_v)
     assert np.array_equal(f.cpu().numpy().view(np.uint64), want_f)
+
+
+def test_first_queries_from_several_threads(pkg, orc):
+    """The query index is built by the first query; four host threads querying
+    one object at once all get the oracle's ranks."""
+    import threading
+
+    keys = inp.distinct_u64(60000, 515)
+    m = pkg.shk_build(keys, 32, 2000)
+    lo, hi = orc.fingerprints_u64(keys)
+    want = orc.query(m.serialize(), lo, hi)
+    out = [None] * 4
+
+    def work(i):
+        out[i] = m.query(keys)
+
+    ts = [threading.Thread(target=work, args=(i,)) for i in range(4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for r in out:
+        assert np.array_equal(r, want)
+    m.close()
