@@ -472,3 +472,37 @@ def test_first_queries_from_several_threads(pkg, orc):
     for r in out:
         assert np.array_equal(r, want)
     m.close()
+
+
+def _mask(bits):
+    return int(sum(int(b) << k for k, b in enumerate(bits)))
+
+
+@pytest.mark.parametrize("rf", [False, True])
+def test_full_leaf_batch(pkg, orc, rf):
+    """The whole 65,536-leaf batch (sizes 40..64, stream seed 3) in the launch
+    the bench times: every leaf's value gives an orientable graph and its f
+    mask is the oracle's canonical orientation; the 8 leaves with the smallest
+    values and 8 leaves of at most 42 keys get the oracle's minimal values."""
+    import torch
+
+    keys, offs = inp.leaf_instances(65536, 3)
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    doff = torch.from_numpy(offs.view(np.int32)).cuda()
+    if rf:
+        vals, fm = pkg.shk_leaf_search_rf(dk, doff)
+    else:
+        vals, fm = pkg.shk_leaf_search(dk, doff, 0)
+    v = vals.cpu().numpy().view(np.uint64)
+    f = fm.cpu().numpy().view(np.uint64)
+    o = offs.astype(np.int64)
+    for i in range(o.size - 1):
+        x = keys[o[i]:o[i + 1]]
+        want = orc.orient_mode(x, int(v[i]), rf)  # raises if the graph is not orientable
+        assert _mask(want) == int(f[i]), i
+    sizes = np.diff(o)
+    pick = list(np.argsort(v)[:8]) + list(np.nonzero(sizes <= 42)[0][:8])
+    packed = np.concatenate([keys[o[i]:o[i + 1]] for i in pick])
+    po = np.zeros(len(pick) + 1, np.uint32)
+    po[1:] = np.cumsum([sizes[i] for i in pick])
+    assert np.array_equal(orc.leaf_search_batch(packed, po, 0, rf=rf)[0], v[pick])
