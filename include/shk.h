@@ -139,7 +139,7 @@ shk_status shk_build_stats(const shk_mphf* mphf, shk_stats* out);
  * For keys of the build set the ranks are a permutation of [0, N); for other
  * keys the result is some value in [0, N) (retrieval semantics, Sec. 2).
  * The first query on an object decodes its tree codes once into a device-side
- * query index (16 bytes per code, about 0.4 bytes per key at leaf size 48;
+ * query index (16 bytes per code, about 0.5 bytes per key at leaf size 48;
  * freed by shk_free) and waits for it; later queries, also from other host
  * threads, use it.  Queries on one object may run concurrently. */
 shk_status shk_query(const shk_mphf* mphf, const shk_keys* keys, uint64_t* ranks_out,
