@@ -305,8 +305,7 @@ __global__ void __launch_bounds__(WARPS * 32)
   if (lane == 0) atomicAdd(executed, done_seeds);
 }
 
-// Throughput probe for the tuner: every warp searches fixed seed ranges of a
-// synthetic leaf of m keys and counts the seeds it evaluated.
+// Keys of the tuner's synthetic leaves.
 __global__ void k_probe_keys(uint64_t* keys, uint64_t n, uint64_t salt) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) keys[i] = mix64(salt + i * 0x9E3779B97F4A7C15ull);
@@ -493,12 +492,11 @@ shk_status tuned_leaf_cfg(Ctx& c, uint32_t m, LeafCfg* out) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   TuneSlot& slot = g_tune[c.device][bin];
   if (!slot.done) {
-    // Every configuration at its best of 3 probe launches.  The probe is a
-    // steady state with every warp busy; in a build, smaller blocks also
-    // finish the last leaves with less idle time (measured on 10^6-key
-    // builds: 8- and 4-warp blocks 3 % faster than 16-warp blocks that probe
-    // within 0.3 %), so among the configurations within 1 % of the best rate
-    // the one with the fewest warps per block is taken.
+    // Every configuration at its best of 3 probe launches.  Among those within
+    // 1 % of the best rate the one with the fewest warps per block is taken:
+    // in a build, smaller blocks leave less SM time idle while the last
+    // leaves finish (measured on 10^6-key builds: 8- and 4-warp blocks 3 %
+    // faster than 16-warp blocks of nearly the same probe rate).
     double rate[kNumLeafCfg], top = 0;
     for (int i = 0; i < kNumLeafCfg; i++) {
       SHK_TRY(probe_leaf_cfg(c, kLeafTable[i].cfg, rep, &rate[i], 3));
