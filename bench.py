@@ -124,23 +124,31 @@ def max_over_ranks(seconds: float, dist, device) -> float:
     return float(t.item())
 
 
-def _cpu_baseline(sample_keys: int, reps: int = 1):
+def _cpu_baseline(sample_keys: int, reps: int = 1, single_keys: int = 0):
     """The oracle as it stands on the host cores, on the first sample_keys keys
-    of the same stream (same leaf and bucket size)."""
+    of the same stream (same leaf and bucket size).  With single_keys > 0 it is
+    also timed on one thread over the first single_keys keys."""
     import oracle
 
     oracle.build()
     import shk_inputs
 
-    keys = shk_inputs.distinct_u64(sample_keys, KEY_SEED)
+    keys = shk_inputs.distinct_u64(max(sample_keys, single_keys), KEY_SEED)
     cores = os.cpu_count() or 1
     t = time.perf_counter()
     for _ in range(reps):
-        oracle.build_mphf(keys, n=LEAF, b=BUCKET, nthreads=cores)
+        oracle.build_mphf(keys[:sample_keys], n=LEAF, b=BUCKET, nthreads=cores)
     dt = time.perf_counter() - t
-    return {"value": sample_keys * reps / dt, "unit": "keys/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {sample_keys} keys of the same stream ({(sample_keys + BUCKET - 1) // BUCKET} buckets), "
-                      f"leaf 48, bucket 2000, OpenMP over buckets, {reps} build(s), {dt:.1f} s"}
+    out = {"value": sample_keys * reps / dt, "unit": "keys/s", "cores": cores, "kind": "oracle",
+           "sample": f"first {sample_keys} keys of the same stream ({(sample_keys + BUCKET - 1) // BUCKET} buckets), "
+                     f"leaf 48, bucket 2000, OpenMP over buckets, {reps} build(s), {dt:.1f} s"}
+    if single_keys:
+        t = time.perf_counter()
+        oracle.build_mphf(keys[:single_keys], n=LEAF, b=BUCKET, nthreads=1)
+        dt1 = time.perf_counter() - t
+        out["single_thread"] = {"value": single_keys / dt1, "unit": "keys/s",
+                                "sample": f"first {single_keys} keys, one thread, {dt1:.1f} s"}
+    return out
 
 
 def run_reference(args):
@@ -327,7 +335,7 @@ def run_ours(args):
     if clocks:
         line["clocks"] = clocks
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline(24000)
+        line["cpu_baseline"] = _cpu_baseline(24000, single_keys=4000)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
