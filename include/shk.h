@@ -268,7 +268,9 @@ shk_status shk_server_submit(shk_server* srv, const shk_keys* keys, const shk_bu
 shk_status shk_server_poll(shk_server* srv, uint64_t req_id, shk_mphf** out,
                            shk_request_info* info);
 
-/* shk_server_wait -- as shk_server_poll, blocking until the request is done. */
+/* shk_server_wait -- as shk_server_poll, blocking until the request is done.
+ * If another thread collects the same request first, SHK_EINVAL (unknown
+ * request id). */
 shk_status shk_server_wait(shk_server* srv, uint64_t req_id, shk_mphf** out,
                            shk_request_info* info);
 
@@ -276,7 +278,8 @@ shk_status shk_server_wait(shk_server* srv, uint64_t req_id, shk_mphf** out,
 shk_status shk_server_get_stats(shk_server* srv, shk_server_stats* out);
 
 /* shk_server_destroy -- finish running builds, drop queued ones, free results
- * never polled.  NULL is ignored. */
+ * never polled.  No other call on srv may be in progress or follow.  NULL is
+ * ignored. */
 void shk_server_destroy(shk_server* srv);
 
 /* shk_version -- format version string ("SHKRS001"). */

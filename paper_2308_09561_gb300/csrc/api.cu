@@ -340,7 +340,7 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
 
   // the encoded object
   shk_mphf* m = new shk_mphf();
-  SHK_CUDA(cudaGetDevice(&m->device));
+  m->device = c.device;
   const uint32_t lK = ef_low_bits(N, B + 1), lO = ef_low_bits(h_rice_bits, B + 1);
   const uint64_t hdr[kHeaderWords] = {kMagic, N, n, b, B, S, eps, num_shards, h_rice_bits, lK,
                                       (N >> lK) + B + 1, lO, (h_rice_bits >> lO) + B + 1,
@@ -431,7 +431,7 @@ extern "C" shk_status shk_build(const shk_keys* keys, const shk_build_opts* opts
   if (!out || !opts) return fail(SHK_EINVAL, "NULL argument");
   *out = nullptr;
   g_last_error.clear();
-  shk_status st = build_impl(keys, opts, (cudaStream_t)cuda_stream, out);
+  shk_status st = no_throw([&] { return build_impl(keys, opts, (cudaStream_t)cuda_stream, out); });
   if (st != SHK_OK) cudaStreamSynchronize((cudaStream_t)cuda_stream);
   return st;
 }
@@ -455,7 +455,7 @@ extern "C" shk_status shk_serialize(const shk_mphf* m, uint8_t* buf, size_t cap,
   return SHK_OK;
 }
 
-extern "C" shk_status shk_deserialize(const uint8_t* buf, size_t len, shk_mphf** out) {
+static shk_status deserialize_impl(const uint8_t* buf, size_t len, shk_mphf** out) {
   if (!buf || !out) return fail(SHK_EINVAL, "NULL argument");
   *out = nullptr;
   if (len < kHeaderWords * 8 || len % 8) return fail(SHK_EFORMAT, "bad length");
@@ -559,7 +559,7 @@ static shk_status ensure_qindex(Ctx& c, shk_mphf* m) {
   return SHK_OK;
 }
 
-extern "C" shk_status shk_query(const shk_mphf* m, const shk_keys* keys, uint64_t* ranks_out,
+static shk_status query_impl(const shk_mphf* m, const shk_keys* keys, uint64_t* ranks_out,
                                 int out_on_device, void* cuda_stream) {
   if (!m || !ranks_out) return fail(SHK_EINVAL, "NULL argument");
   SHK_TRY(check_keys(keys));
@@ -625,7 +625,7 @@ struct LeafGraph {
 static thread_local LeafGraph g_leaf_graph;
 static thread_local cudaStream_t g_capture_stream[64];
 
-extern "C" shk_status shk_leaf_search(const uint64_t* leaf_keys, const uint32_t* leaf_off,
+static shk_status leaf_search_impl(const uint64_t* leaf_keys, const uint32_t* leaf_off,
                                       uint32_t n_leaves, uint64_t seed_start, uint64_t* seeds_out,
                                       uint64_t* f_out, void* cuda_stream) {
   if (n_leaves && (!leaf_keys || !leaf_off || !seeds_out)) return fail(SHK_EINVAL, "NULL argument");
@@ -717,7 +717,7 @@ extern "C" shk_status shk_leaf_search(const uint64_t* leaf_keys, const uint32_t*
 
 extern "C" uint64_t shk_leaf_graph_replays(void) { return g_leaf_graph.replays; }
 
-extern "C" shk_status shk_leaf_search_rf(const uint64_t* leaf_keys, const uint32_t* leaf_off,
+static shk_status leaf_search_rf_impl(const uint64_t* leaf_keys, const uint32_t* leaf_off,
                                          uint32_t n_leaves, uint64_t* values_out, uint64_t* f_out,
                                          void* cuda_stream) {
   if (n_leaves && (!leaf_keys || !leaf_off || !values_out)) return fail(SHK_EINVAL, "NULL argument");
@@ -751,7 +751,7 @@ extern "C" shk_status shk_leaf_search_rf(const uint64_t* leaf_keys, const uint32
   return s;
 }
 
-extern "C" shk_status shk_leaf_tune(uint32_t leaf_size, uint32_t* cfg_out, double* evals_per_s,
+static shk_status leaf_tune_impl(uint32_t leaf_size, uint32_t* cfg_out, double* evals_per_s,
                                     int probe_all, double* all_evals_per_s) {
   if (leaf_size < 2 || leaf_size > kMaxLeaf || !cfg_out) return fail(SHK_EINVAL, "bad argument");
   Ctx c(nullptr);
@@ -778,4 +778,35 @@ extern "C" uint32_t shk_leaf_configs(uint32_t* cfgs, uint32_t cap) {
     cfgs[4 * i + 3] = c.passes;
   }
   return n;
+}
+
+// C entry points over the implementations above; no host exception escapes.
+extern "C" shk_status shk_deserialize(const uint8_t* buf, size_t len, shk_mphf** out) {
+  return no_throw([&] { return deserialize_impl(buf, len, out); });
+}
+
+extern "C" shk_status shk_query(const shk_mphf* m, const shk_keys* keys, uint64_t* ranks_out,
+                                int out_on_device, void* cuda_stream) {
+  return no_throw([&] { return query_impl(m, keys, ranks_out, out_on_device, cuda_stream); });
+}
+
+extern "C" shk_status shk_leaf_search(const uint64_t* leaf_keys, const uint32_t* leaf_off,
+                                      uint32_t n_leaves, uint64_t seed_start, uint64_t* seeds_out,
+                                      uint64_t* f_out, void* cuda_stream) {
+  return no_throw([&] {
+    return leaf_search_impl(leaf_keys, leaf_off, n_leaves, seed_start, seeds_out, f_out, cuda_stream);
+  });
+}
+
+extern "C" shk_status shk_leaf_search_rf(const uint64_t* leaf_keys, const uint32_t* leaf_off,
+                                         uint32_t n_leaves, uint64_t* values_out, uint64_t* f_out,
+                                         void* cuda_stream) {
+  return no_throw([&] {
+    return leaf_search_rf_impl(leaf_keys, leaf_off, n_leaves, values_out, f_out, cuda_stream);
+  });
+}
+
+extern "C" shk_status shk_leaf_tune(uint32_t leaf_size, uint32_t* cfg_out, double* evals_per_s,
+                                    int probe_all, double* all_evals_per_s) {
+  return no_throw([&] { return leaf_tune_impl(leaf_size, cfg_out, evals_per_s, probe_all, all_evals_per_s); });
 }

@@ -11,6 +11,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -113,40 +114,43 @@ struct shk_server {
 
 using namespace shk;
 
-extern "C" shk_status shk_server_create(uint64_t hbm_budget_bytes, uint32_t workers,
-                                        shk_server** out) {
-  if (!out) return fail(SHK_EINVAL, "NULL argument");
-  *out = nullptr;
-  shk_server* s = new shk_server();
-  if (cudaGetDevice(&s->device) != cudaSuccess) {
-    delete s;
-    return fail(SHK_ECUDA, "cudaGetDevice failed");
-  }
+static shk_status server_create(uint64_t hbm_budget_bytes, uint32_t workers, shk_server** out) {
+  std::unique_ptr<shk_server> s(new shk_server());
+  if (cudaGetDevice(&s->device) != cudaSuccess) return fail(SHK_ECUDA, "cudaGetDevice failed");
   if (hbm_budget_bytes == 0) {
     size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-      delete s;
-      return fail(SHK_ECUDA, "cudaMemGetInfo failed");
-    }
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(SHK_ECUDA, "cudaMemGetInfo failed");
     hbm_budget_bytes = (uint64_t)(free_b * 0.8);
   }
   s->budget = hbm_budget_bytes;
   const uint32_t w = workers ? workers : 4;
-  for (uint32_t i = 0; i < w; i++) s->threads.emplace_back([s] { s->worker(); });
-  *out = s;
+  shk_server* raw = s.get();
+  try {
+    for (uint32_t i = 0; i < w; i++) s->threads.emplace_back([raw] { raw->worker(); });
+  } catch (...) {
+    shk_server_destroy(s.release());  // stops and joins the workers already started
+    throw;
+  }
+  *out = s.release();
   return SHK_OK;
 }
 
-extern "C" shk_status shk_server_submit(shk_server* srv, const shk_keys* keys,
-                                        const shk_build_opts* opts, uint64_t* req_id) {
-  if (!srv || !keys || !opts || !req_id) return fail(SHK_EINVAL, "NULL argument");
+extern "C" shk_status shk_server_create(uint64_t hbm_budget_bytes, uint32_t workers,
+                                        shk_server** out) {
+  if (!out) return fail(SHK_EINVAL, "NULL argument");
+  *out = nullptr;
+  return no_throw([&] { return server_create(hbm_budget_bytes, workers, out); });
+}
+
+static shk_status server_submit(shk_server* srv, const shk_keys* keys, const shk_build_opts* opts,
+                                uint64_t* req_id) {
   if (keys->kind != SHK_KEYS_U64 && keys->kind != SHK_KEYS_STR && keys->kind != SHK_KEYS_FP128)
     return fail(SHK_EINVAL, "unknown key kind");
   const uint64_t N = keys->n_keys;
   if (N && !keys->data) return fail(SHK_EINVAL, "key data is NULL");
   if (keys->kind == SHK_KEYS_STR && N && !keys->str_offsets)
     return fail(SHK_EINVAL, "string keys need str_offsets");
-  Request* r = new Request();
+  std::unique_ptr<Request> r(new Request());
   r->kind = keys->kind;
   r->n_keys = N;
   r->opts = *opts;
@@ -156,13 +160,11 @@ extern "C" shk_status shk_server_submit(shk_server* srv, const shk_keys* keys,
   if (keys->kind == SHK_KEYS_STR) {
     r->offsets.resize(N + 1);
     if (cudaMemcpy(r->offsets.data(), keys->str_offsets, (N + 1) * 8, dir) != cudaSuccess) {
-      delete r;
       return fail(SHK_ECUDA, "copying string offsets failed");
     }
     const uint64_t base = r->offsets[0], total = r->offsets[N] - base;
     r->data.resize(total + 8);
     if (total && cudaMemcpy(r->data.data(), (const uint8_t*)keys->data + base, total, dir) != cudaSuccess) {
-      delete r;
       return fail(SHK_ECUDA, "copying string keys failed");
     }
     for (auto& v : r->offsets) v -= base;
@@ -170,31 +172,48 @@ extern "C" shk_status shk_server_submit(shk_server* srv, const shk_keys* keys,
     const uint64_t bytes = N * (keys->kind == SHK_KEYS_U64 ? 8 : 16);
     r->data.resize(bytes ? bytes : 8);
     if (bytes && cudaMemcpy(r->data.data(), keys->data, bytes, dir) != cudaSuccess) {
-      delete r;
       return fail(SHK_ECUDA, "copying keys failed");
     }
   }
   r->info.n_keys = N;
   r->info.footprint_bytes = footprint(N, *opts, r->data.size());
   r->info.submit_ns = now_ns();
-  {
+  const uint64_t id = [&] {
     std::lock_guard<std::mutex> lk(srv->mu);
     r->id = srv->next_id++;
-    srv->all[r->id] = r;
-    srv->queue.push_back(r);
+    srv->all[r->id] = r.get();
+    try {
+      srv->queue.push_back(r.get());
+    } catch (...) {
+      srv->all.erase(r->id);
+      throw;
+    }
     srv->submitted++;
-  }
+    return r.release()->id;
+  }();
   srv->cv_work.notify_all();
-  *req_id = r->id;
+  *req_id = id;
   return SHK_OK;
+}
+
+extern "C" shk_status shk_server_submit(shk_server* srv, const shk_keys* keys,
+                                        const shk_build_opts* opts, uint64_t* req_id) {
+  if (!srv || !keys || !opts || !req_id) return fail(SHK_EINVAL, "NULL argument");
+  return no_throw([&] { return server_submit(srv, keys, opts, req_id); });
 }
 
 static shk_status poll_locked(shk_server* srv, uint64_t req_id, shk_mphf** out,
                               shk_request_info* info, std::unique_lock<std::mutex>& lk, bool wait) {
+  // A waiter looks the request up again after every wake-up: another thread
+  // may have collected (and freed) it meanwhile.
   auto it = srv->all.find(req_id);
+  if (wait)
+    srv->cv_done.wait(lk, [&] {
+      it = srv->all.find(req_id);
+      return it == srv->all.end() || it->second->info.done != 0;
+    });
   if (it == srv->all.end()) return fail(SHK_EINVAL, "unknown request id");
   Request* r = it->second;
-  if (wait) srv->cv_done.wait(lk, [&] { return r->info.done != 0; });
   if (info) *info = r->info;
   if (out) *out = nullptr;
   if (!r->info.done) return SHK_OK;

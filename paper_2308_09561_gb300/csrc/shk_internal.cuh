@@ -8,7 +8,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <exception>
 #include <mutex>
+#include <new>
 #include <string>
 
 #include "../../include/shk.h"
@@ -200,6 +202,19 @@ struct LeafDesc {
 // ---------------------------------------------------------------------------
 void set_error(const std::string& msg);
 shk_status fail(shk_status st, const std::string& msg);
+
+// Runs f, turning a host-side exception (a failed host allocation, a thread
+// that cannot start) into a status: no exception crosses the C ABI.
+template <class F>
+shk_status no_throw(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return fail(SHK_ENOMEM, "host memory allocation failed");
+  } catch (const std::exception& e) {
+    return fail(SHK_ENOMEM, e.what());
+  }
+}
 
 #define SHK_CUDA(call)                                                          \
   do {                                                                          \

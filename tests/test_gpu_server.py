@@ -115,3 +115,32 @@ def test_concurrent_builds_with_different_shared_memory_needs(pkg):
             assert m.serialize() == alone[i]
     finally:
         pkg.shk_server_destroy(srv)
+
+
+def test_several_threads_waiting_on_one_request(pkg):
+    """Four threads wait on the same request: exactly one collects the MPHF,
+    the others learn that the id is no longer known."""
+    import threading
+
+    keys = inp.distinct_u64(200000, 33)
+    want = pkg.shk_build(keys, 32, 2000).serialize()
+    srv = pkg.shk_server_create(0, 1)
+    got, errors = [], []
+
+    def waiter(rid):
+        try:
+            got.append(pkg.shk_server_wait(srv, rid)[0].serialize())
+        except pkg.ShkError as e:
+            errors.append(e.status)
+
+    try:
+        rid = pkg.shk_server_submit(srv, keys, 32, 2000)
+        ts = [threading.Thread(target=waiter, args=(rid,)) for _ in range(4)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        assert got == [want]
+        assert errors == [pkg.SHK_EINVAL] * 3
+    finally:
+        pkg.shk_server_destroy(srv)
