@@ -149,16 +149,23 @@ def _as_keys(keys, kind: int, str_offsets=None):
         keep.append(t)
         k.on_device = 1 if t.is_cuda else 0
         k.data = t.data_ptr() if t.numel() else None
-        nbytes = t.numel() * t.element_size()
+        nbytes, itemsize = t.numel() * t.element_size(), t.element_size()
     else:
         a = np.ascontiguousarray(keys)
         keep.append(a)
         k.on_device = 0
         k.data = a.ctypes.data if a.size else None
-        nbytes = a.nbytes
+        nbytes, itemsize = a.nbytes, a.itemsize
+    want = {SHK_KEYS_U64: 8, SHK_KEYS_FP128: 8, SHK_KEYS_STR: 1}.get(kind)
+    if want is None:
+        raise ValueError(f"unknown key kind {kind}")
+    if itemsize != want:
+        raise ValueError(f"key kind {kind} takes {want}-byte elements, got {itemsize}-byte ones")
     if kind == SHK_KEYS_U64:
         k.n_keys = nbytes // 8
     elif kind == SHK_KEYS_FP128:
+        if nbytes % 16:
+            raise ValueError("128-bit fingerprints need an even number of 64-bit words")
         k.n_keys = nbytes // 16
     else:
         if isinstance(str_offsets, torch.Tensor):

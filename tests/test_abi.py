@@ -62,3 +62,24 @@ def test_host_side_argument_errors_without_gpu(lib):
     with pytest.raises(pkg.ShkError) as e:
         pkg.shk_deserialize(b"\0" * 130)
     assert e.value.status == pkg.SHK_EFORMAT
+
+
+def test_binding_rejects_keys_of_the_wrong_element_size():
+    """The binding describes keys by their bytes; an array of another element
+    size is refused rather than reinterpreted."""
+    import numpy as np
+
+    import paper_2308_09561_gb300 as pkg
+
+    with pytest.raises(ValueError):
+        pkg._as_keys(np.zeros(4, np.uint32), pkg.SHK_KEYS_U64)
+    with pytest.raises(ValueError):
+        pkg._as_keys(np.zeros(3, np.uint64), pkg.SHK_KEYS_FP128)
+    with pytest.raises(ValueError):
+        pkg._as_keys(np.zeros(8, np.uint64), pkg.SHK_KEYS_STR, np.array([0, 8], np.uint64))
+    with pytest.raises(ValueError):
+        pkg._as_keys(np.zeros(2, np.uint64), 7)
+    k, _ = pkg._as_keys(np.zeros(6, np.uint64), pkg.SHK_KEYS_FP128)
+    assert k.n_keys == 3 and k.on_device == 0
+    k, _ = pkg._as_keys(np.zeros(10, np.uint8), pkg.SHK_KEYS_STR, np.array([0, 4, 10], np.uint64))
+    assert k.n_keys == 2
