@@ -285,6 +285,14 @@ void shk_server_destroy(shk_server* srv);
 /* shk_version -- format version string ("SHKRS001"). */
 const char* shk_version(void);
 
+/* shk_release_memory -- return to the device the working memory the library
+ * keeps between calls.  Builds and queries take their temporary device memory
+ * from a memory pool per device that the library owns; memory freed at the end
+ * of a call stays in that pool (up to the largest call's working set) so that
+ * the next call does not map it again.  Safe while other calls run: only memory
+ * no call holds is released.  MPHF objects are not affected. */
+void shk_release_memory(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ EXPORTS = ("shk_build", "shk_build_stats", "shk_query", "shk_serialize", "shk_de
            "shk_leaf_tune", "shk_leaf_configs", "shk_leaf_graph_replays", "shk_leaf_search_rf",
            "shk_server_create",
            "shk_server_submit", "shk_server_poll", "shk_server_wait", "shk_server_get_stats",
-           "shk_server_destroy", "shk_version")
+           "shk_server_destroy", "shk_version", "shk_release_memory")
 
 
 class ShkError(RuntimeError):
@@ -106,6 +106,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "shk_server_get_stats": (i32, [vp, ctypes.POINTER(_SrvStats)]),
         "shk_server_destroy": (None, [vp]),
         "shk_version": (ctypes.c_char_p, []),
+        "shk_release_memory": (None, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -276,6 +277,11 @@ def shk_deserialize(data: bytes) -> Mphf:
 
 def shk_size_bits(handle) -> int:
     return int(load_library().shk_size_bits(handle))
+
+
+def shk_release_memory() -> None:
+    """Return the library's pooled working memory to the device."""
+    load_library().shk_release_memory()
 
 
 def shk_free(handle) -> None:

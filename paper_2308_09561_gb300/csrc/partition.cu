@@ -342,7 +342,7 @@ constexpr uint32_t kRadixDigits = 512;
 // shift: digit = bucket >> shift; window_bits >= 32: digits counted from 0
 // (pass 1 or the single pass); otherwise from the tile's first key's bucket
 // rounded down to a multiple of 2^window_bits (pass 2).
-__global__ void __launch_bounds__(kRadixThreads)
+__global__ void __launch_bounds__(kRadixThreads, 4)
     k_radix_pass(const ulonglong2* __restrict__ in, uint32_t n, uint64_t B, uint32_t shift,
                  uint32_t window_bits, const uint32_t* __restrict__ K, uint32_t* cursor,
                  ulonglong2* __restrict__ out) {
@@ -351,6 +351,19 @@ __global__ void __launch_bounds__(kRadixThreads)
   __shared__ uint32_t wsum[kRadixThreads / 32];
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t tiles = (n + kRadixTile - 1) / kRadixTile;
+  // The next tile's records are loaded into registers while the current
+  // tile's staged runs are written out.
+  ulonglong2 v[kRadixPerThread];
+  auto load_tile = [&](uint32_t tt) {
+    const uint32_t b = tt * kRadixTile;
+    const uint32_t c = n - b < kRadixTile ? n - b : kRadixTile;
+#pragma unroll
+    for (int k = 0; k < kRadixPerThread; k++) {
+      const uint32_t i = k * kRadixThreads + tid;
+      if (i < c) v[k] = in[b + i];
+    }
+  };
+  if (blockIdx.x < tiles) load_tile(blockIdx.x);
   for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const uint32_t base = t * kRadixTile;
     const uint32_t cnt = n - base < kRadixTile ? n - base : kRadixTile;
@@ -358,14 +371,12 @@ __global__ void __launch_bounds__(kRadixThreads)
     const uint64_t dbase =
         window_bits >= 32 ? 0 : ((mulhi64(in[base].y, B) >> window_bits) << window_bits);
     __syncthreads();
-    ulonglong2 v[kRadixPerThread];
     uint32_t dg[kRadixPerThread], rk[kRadixPerThread];
 #pragma unroll
     for (int k = 0; k < kRadixPerThread; k++) {
       const uint32_t i = k * kRadixThreads + tid;
       dg[k] = kRadixDigits;
       if (i < cnt) {
-        v[k] = in[base + i];
         const uint64_t da = mulhi64(v[k].y, B) >> shift;
         if (da - dbase < kRadixDigits) {
           dg[k] = (uint32_t)(da - dbase);
@@ -406,6 +417,7 @@ __global__ void __launch_bounds__(kRadixThreads)
     for (int k = 0; k < kRadixPerThread; k++)
       if (dg[k] < kRadixDigits) stage[lstart[dg[k]] + rk[k]] = v[k];
     __syncthreads();
+    if (t + gridDim.x < tiles) load_tile(t + gridDim.x);
     // contiguous runs: consecutive threads write consecutive records
     const uint32_t staged = lstart[kRadixDigits - 1] + hist[kRadixDigits - 1];
     for (uint32_t i = tid; i < staged; i += kRadixThreads) {

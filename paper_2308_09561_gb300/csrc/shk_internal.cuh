@@ -229,6 +229,10 @@ shk_status no_throw(F&& f) {
     if (s_ != SHK_OK) return s_;         \
   } while (0)
 
+// Stream-ordered allocation from the library's memory pool of the current
+// device (created on first use; it keeps freed memory for later calls).
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s);
+
 // Stream-ordered device allocations that are released together.
 struct Arena {
   cudaStream_t stream;
@@ -242,8 +246,8 @@ struct Arena {
   shk_status alloc(T** p, size_t count, bool zero = false) {
     void* q = nullptr;
     size_t bytes = count ? count * sizeof(T) : 16;
-    cudaError_t e = cudaMallocAsync(&q, bytes, stream);
-    if (e != cudaSuccess) return fail(SHK_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    cudaError_t e = pool_malloc(&q, bytes, stream);
+    if (e != cudaSuccess) return fail(SHK_ENOMEM, std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e));
     if (n < 128) ptrs[n++] = q;
     if (zero) {
       e = cudaMemsetAsync(q, 0, bytes, stream);

@@ -474,6 +474,28 @@ def test_first_queries_from_several_threads(pkg, orc):
     m.close()
 
 
+def test_pooled_working_memory_is_kept_and_released(pkg):
+    """A build's working memory stays in the library's pool after the build
+    (the next build does not map it again) and shk_release_memory returns it;
+    results do not depend on either."""
+    import torch
+
+    d = _dev(inp.distinct_u64(4_000_000, 516))
+    pkg.shk_release_memory()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    m = pkg.shk_build(d, 48, 2000, leaf_mode=pkg.SHK_LEAF_ROTATION)
+    want = m.serialize()
+    m.close()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 < free0 - (100 << 20)
+    pkg.shk_release_memory()
+    free2 = torch.cuda.mem_get_info()[0]
+    assert free2 > free1 + (100 << 20)
+    assert pkg.shk_build(d, 48, 2000, leaf_mode=pkg.SHK_LEAF_ROTATION).serialize() == want
+
+
 def _mask(bits):
     return int(sum(int(b) << k for k, b in enumerate(bits)))
 
