@@ -342,6 +342,8 @@ constexpr uint32_t kRadixDigits = 512;
 // shift: digit = bucket >> shift; window_bits >= 32: digits counted from 0
 // (pass 1 or the single pass); otherwise from the tile's first key's bucket
 // rounded down to a multiple of 2^window_bits (pass 2).
+// Capped at 64 registers (4 blocks per SM): holding the next tile in registers
+// must not cost resident blocks.
 __global__ void __launch_bounds__(kRadixThreads, 4)
     k_radix_pass(const ulonglong2* __restrict__ in, uint32_t n, uint64_t B, uint32_t shift,
                  uint32_t window_bits, const uint32_t* __restrict__ K, uint32_t* cursor,
