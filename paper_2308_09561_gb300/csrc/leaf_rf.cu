@@ -89,22 +89,28 @@ __device__ __forceinline__ void rf_rotations8(uint64_t ma, const uint64_t* mb, u
       rl[u] = ~0u;
       rh[u] = ~0u;
     }
-    for (int it = 0; it < kHalf && zl; it++) {
+    // two cells per step (a lone last cell is taken twice: the AND is
+    // idempotent), so each seed's pair of words takes one three-input AND
+    for (int it = 0; it < kHalf / 2 && zl; it++) {
       const uint32_t c = __ffs(zl) - 1;
+      zl &= zl - 1;
+      const uint32_t d = zl ? __ffs(zl) - 1 : c;
       zl &= zl - 1;
 #pragma unroll
       for (int u = 0; u < kRfSeeds; u++) {
-        rh[u] &= __funnelshift_l(bl[u], bh[u], c);
-        rl[u] &= __funnelshift_l(bh[u], bl[u], c);
+        rh[u] &= __funnelshift_l(bl[u], bh[u], c) & __funnelshift_l(bl[u], bh[u], d);
+        rl[u] &= __funnelshift_l(bh[u], bl[u], c) & __funnelshift_l(bh[u], bl[u], d);
       }
     }
-    for (int it = 0; it < kHalf && zh; it++) {
+    for (int it = 0; it < kHalf / 2 && zh; it++) {
       const uint32_t c = __ffs(zh) - 1;
+      zh &= zh - 1;
+      const uint32_t d = zh ? __ffs(zh) - 1 : c;
       zh &= zh - 1;
 #pragma unroll
       for (int u = 0; u < kRfSeeds; u++) {
-        rh[u] &= __funnelshift_l(bh[u], bl[u], c);
-        rl[u] &= __funnelshift_l(bl[u], bh[u], c);
+        rh[u] &= __funnelshift_l(bh[u], bl[u], c) & __funnelshift_l(bh[u], bl[u], d);
+        rl[u] &= __funnelshift_l(bl[u], bh[u], c) & __funnelshift_l(bl[u], bh[u], d);
       }
     }
 #pragma unroll
