@@ -155,7 +155,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    sample = 24000
+    sample = args.ref_sample_keys
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state; warm-up steps would only add minutes
     t = time.perf_counter()
@@ -580,6 +580,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample-keys", type=int, default=24000,
+                    help="reference arm: keys of the workload's stream the oracle builds per step")
     ap.add_argument("--keys", type=int, default=None,
                     help="key (leafbatch: leaf) count other than the workload's own, for profiling runs")
     ap.add_argument("--compare-per-bucket", action="store_true",
