@@ -83,3 +83,39 @@ def test_binding_rejects_keys_of_the_wrong_element_size():
     assert k.n_keys == 3 and k.on_device == 0
     k, _ = pkg._as_keys(np.zeros(10, np.uint8), pkg.SHK_KEYS_STR, np.array([0, 4, 10], np.uint64))
     assert k.n_keys == 2
+
+
+def test_missing_library_raises():
+    """Without the built library every call raises: there is no fallback."""
+    import subprocess
+    import sys
+
+    code = ("import paper_2308_09561_gb300 as p\n"
+            "try:\n"
+            "    p.load_library('/nonexistent/libshk_gpu.so')\n"
+            "except p.ShkError as e:\n"
+            "    print('raised', e.status)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "raised 4"
+
+
+def test_compute_calls_fail_loudly_without_a_device(lib):
+    """On a machine without a CUDA device a build raises (the stream lookup or
+    the library reports the missing device) instead of computing anything
+    elsewhere; with an explicit stream handle the library itself reports
+    SHK_ECUDA."""
+    import numpy as np
+    import torch
+
+    import paper_2308_09561_gb300 as pkg
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    pkg.load_library()
+    keys = np.arange(1, 1001, dtype=np.uint64)
+    with pytest.raises(RuntimeError):
+        pkg.shk_build(keys, 16, 100)
+    with pytest.raises(pkg.ShkError) as e:
+        pkg.shk_build(keys, 16, 100, stream=0)
+    assert e.value.status == pkg.SHK_ECUDA
