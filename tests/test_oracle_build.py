@@ -89,6 +89,15 @@ def test_format_sections_decode(orc):
     assert h["efK_hi_bits"] == (int(K[-1]) >> h["efK_l"]) + B + 1
     O = bl.O()
     assert O[0] == 0 and O[-1] == h["rice_bits"]
+    # the same Elias-Fano parameters for the Rice bit offsets; with
+    # l = floor(log2(U / (B + 1))) the high parts take fewer than 3 (B + 1)
+    # bits, so a sequence takes fewer than (B + 1)(l + 3) bits
+    qo = int(O[-1]) // (B + 1)
+    assert h["efO_l"] == (qo.bit_length() - 1 if qo else 0)
+    assert h["efO_hi_bits"] == (int(O[-1]) >> h["efO_l"]) + B + 1
+    for l_name, hi_name in (("efK_l", "efK_hi_bits"), ("efO_l", "efO_hi_bits")):
+        assert (B + 1) * h[l_name] + h[hi_name] < (B + 1) * (h[l_name] + 3)
+    assert np.all(np.diff(O.astype(np.int64)) >= 0)
     order = np.lexsort((lo, hi))
     for i in range(B):
         sel = order[K[i]:K[i + 1]]
