@@ -285,10 +285,9 @@ def _leaves(orc, m, n):
     return out
 
 
-def test_tree_shape_example_n64():
+def test_tree_shape_example_n64(orc):
     """Fanouts 4 (lowest) and 3 (next) for n > 24, binary splits above."""
-    import oracle
-
+    oracle = orc
     assert oracle.split_shape(2000, 64) == (1536, 2)
     assert oracle.split_shape(1536, 64) == (768, 2)
     assert oracle.split_shape(768, 64) == (256, 3)
@@ -346,12 +345,18 @@ def test_split_trials_match_multinomial(orc, m, n, count):
 
 
 def test_split_seed_is_minimum(orc):
+    """Sec. 2 RecSplit: the split seed gives the prescribed part sizes and no
+    smaller seed does."""
     for t in range(30):
         m, n = 40, 10
         unit, fan = orc.split_shape(m, n)
         parts = [unit] * (fan - 1) + [m - (fan - 1) * unit]
         x = inp.splitmix64_stream(90000 + t, m)
         s = orc.split_seed(x, n)
+        cnt = [0] * fan
+        for v in x:
+            cnt[orc.split_child(int(v), s, m, unit, fan)] += 1
+        assert cnt == parts
         for s2 in range(s):
             cnt = [0] * fan
             for v in x:
@@ -359,9 +364,19 @@ def test_split_seed_is_minimum(orc):
             assert cnt != parts
 
 
-def test_rice_parameters():
-    import oracle
+def test_leaf_rice_table_follows_its_closed_form(orc):
+    """The frozen leaf Rice parameters are floor(log2(ln2 * T_m)) with
+    T_m = 0.8 (e/2)^m e / sqrt(pi m): the trial bound of Thm.
+    shockHashConstruction divided by sqrt(m), as Sec. 8.1 observes (every
+    value is at least 0.012 away from an integer, so float evaluation is
+    exact here)."""
+    for m in range(2, 65):
+        t = 0.8 * (math.e / 2) ** m * math.e / math.sqrt(math.pi * m)
+        assert orc.rice_k_leaf(m) == max(0, math.floor(math.log2(math.log(2) * t))), m
 
+
+def test_rice_parameters(orc):
+    oracle = orc
     assert oracle.rice_k_split(2000, 64) == 5
     assert oracle.rice_k_split(256, 64) == 11
     assert oracle.rice_k_leaf(64) == 25 and oracle.rice_k_leaf(32) == 11
