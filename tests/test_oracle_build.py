@@ -220,6 +220,43 @@ def test_leaves_made_by_splits_behave_like_random_leaves(orc):
     assert abs(t.mean() - 33.04) < 5 * se + 0.2
 
 
+@pytest.mark.parametrize("n", [4, 24, 40])
+def test_leaf_order_is_the_stable_partition(orc, n):
+    """Sec. 2 RecSplit: a split node sends each key to the child its split
+    hash names, children in order, keys keeping their relative order (so
+    every leaf stays in ascending fingerprint order); codes are in preorder.
+    The leaf order is rederived here from the preorder codes."""
+    keys = inp.distinct_u64(3000, 77)
+    lo, hi = orc.fingerprints_u64(keys)
+    o = np.lexsort((lo, hi))[:900]
+    seeds, _, llo, lhi, _ = orc.bucket_build(lo[o], hi[o], n)
+    codes = iter(int(v) for v in seeds)
+    out = []
+
+    def walk(pairs):
+        m = len(pairs)
+        sh = orc.split_shape(m, n)
+        if sh is None:
+            if m >= 2:
+                next(codes)
+            out.extend(pairs)
+            return
+        unit, fan = sh
+        s = next(codes)
+        child = [orc.split_child(a, s, m, unit, fan) for a, _ in pairs]
+        for j in range(fan):
+            walk([p for p, c in zip(pairs, child) if c == j])
+
+    walk([(int(a), int(b)) for a, b in zip(lo[o], hi[o])])
+    assert next(codes, None) is None
+    assert out == [(int(a), int(b)) for a, b in zip(llo, lhi)]
+    pos = 0
+    for m in _leaf_sizes(orc, len(o), n):
+        leaf = out[pos:pos + m]
+        assert leaf == sorted(leaf, key=lambda p: (p[1], p[0]))
+        pos += m
+
+
 @pytest.mark.parametrize("n", [8, 24, 40])
 def test_splits_only_equals_the_full_bucket_build(orc, n):
     """The splits-only bucket walk gives the full build's split codes, Rice

@@ -31,6 +31,14 @@ MUTANTS = [
     ("bucket: scaled by B - 1",
      "((u128)hi * B) >> 64", "((u128)hi * (B - 1)) >> 64",
      lambda o: build_pins.test_bucket_occupancy_chi_square(o)),
+    ("in-bucket order: lo compared before hi",
+     "  if (x[1] != y[1]) return x[1] < y[1] ? -1 : 1; /* hi first */\n  if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;",
+     "  if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;\n  if (x[1] != y[1]) return x[1] < y[1] ? -1 : 1;",
+     lambda o: build_pins.test_format_sections_decode(o)),
+    ("partition: a child's keys in reverse order",
+     "    for (uint32_t i = 0; i < m; i++)\n      if (orc_split_child(lo[i], s, m, unit, fan) == j) {",
+     "    for (uint32_t i = m; i-- > 0;)\n      if (orc_split_child(lo[i], s, m, unit, fan) == j) {",
+     lambda o: build_pins.test_leaf_order_is_the_stable_partition(o, 24)),
     ("tree shape: one part too many",
      "*fanout = (m + n - 1) / n;", "*fanout = (m + n) / n;",
      lambda o: pins.test_tree_shape_example_n64(o)),
