@@ -78,6 +78,15 @@ MUTANTS = [
     ("retrieval: band start range one slot short",
      "*start = (uint64_t)(((u128)u * (m - 63)) >> 64);", "*start = (uint64_t)(((u128)u * (m - 64)) >> 64);",
      lambda o: pins.test_ribbon_canonical_solution(o, 60, 3277)),
+    ("retrieval: orientation bits stored inverted",
+     "    uint8_t b = f[i];", "    uint8_t b = f[i] ^ 1u;",
+     lambda o: build_pins.test_build_is_bijection(o, 3000, 8, 100)),
+    ("Elias-Fano: low parts taken one bit too high",
+     "if (!bv_push_bits(low, v[i], l)) return 0;", "if (!bv_push_bits(low, v[i] >> 1, l)) return 0;",
+     lambda o: build_pins.test_format_sections_decode(o)),
+    ("query: a set retrieval bit read as the first cell",
+     "local = bit ? h1 : h0;", "local = bit ? h0 : h1;",
+     lambda o: build_pins.test_build_is_bijection(o, 3000, 8, 100)),
     ("query: skipped subtrees not counted",
      "      offset += p;\n", "\n",
      lambda o: build_pins.test_build_is_bijection(o, 3000, 8, 100)),
