@@ -119,3 +119,18 @@ def test_compute_calls_fail_loudly_without_a_device(lib):
     with pytest.raises(pkg.ShkError) as e:
         pkg.shk_build(keys, 16, 100, stream=0)
     assert e.value.status == pkg.SHK_ECUDA
+
+
+def test_leaf_configuration_table_without_gpu(lib):
+    """The autotuner's configuration table is host data: every entry is a
+    supported shape (seeds per lane 1-4, warps per block a power of two up
+    to 16, key unroll 1-4), and the configuration the tuner picks on GB300
+    for 48-key leaves (4 seeds, 8 warps, unroll 4) is one of them."""
+    import paper_2308_09561_gb300 as pkg
+
+    pkg.load_library()
+    cfgs = pkg.shk_leaf_configs()
+    assert len(cfgs) == len(set(cfgs)) >= 4
+    for u, w, r in cfgs:
+        assert 1 <= u <= 4 and w in (4, 8, 16) and 1 <= r <= 4
+    assert (4, 8, 4) in cfgs
