@@ -134,3 +134,21 @@ def test_leaf_configuration_table_without_gpu(lib):
     for u, w, r in cfgs:
         assert 1 <= u <= 4 and w in (4, 8, 16) and 1 <= r <= 4
     assert (4, 8, 4) in cfgs
+
+
+def test_oracle_and_cuda_path_share_no_code():
+    """The oracle and the CUDA library are independent: neither side imports,
+    includes or builds the other's sources."""
+    import glob as _glob
+
+    pkg_dir = os.path.join(ROOT, "paper_2308_09561_gb300")
+    oracle_dir = os.path.join(ROOT, "oracle")
+    for path in _glob.glob(os.path.join(pkg_dir, "**", "*.*"), recursive=True):
+        if path.endswith((".py", ".cu", ".cuh", ".h", ".c")) and "_build" not in path:
+            text = open(path).read()
+            assert "oracle" not in text.lower(), path
+    for path in _glob.glob(os.path.join(oracle_dir, "*.*")):
+        if path.endswith((".py", ".c", ".h")):
+            text = open(path).read()
+            assert not re.search(r"^\s*(import|from)\s+paper_2308_09561_gb300", text, flags=re.M), path
+            assert not re.search(r'#\s*include\s*"[^"]*(csrc|shk_internal|kernels|shk\.h)', text), path
