@@ -189,10 +189,11 @@ shk_status shk_leaf_search(const uint64_t* leaf_keys, const uint32_t* leaf_off,
  * and output buffer.  Working memory comes from one fixed array in the
  * library's device image (about 1.3 MB, held by every GPU that loads the
  * library until the process exits), so n_leaves is limited to 65536
- * (SHK_EINVAL beyond, with a message).  The first call on a device looks up
- * the array's device address; make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race and
- * must be serialised by the caller. */
+ * (SHK_EINVAL beyond, with a message).  Each call looks up the array's
+ * device address on the current device (no allocation), reads the device
+ * error flag back and synchronises cuda_stream, so it cannot be called inside
+ * a stream capture.  All calls share the array: calls that overlap on the GPU
+ * race and must be serialised by the caller. */
 shk_status shk_leaf_search_noalloc(const uint64_t* leaf_keys, const uint32_t* leaf_off,
                                    uint32_t n_leaves, uint64_t seed_start, uint64_t* seeds_out,
                                    uint64_t* f_out, void* cuda_stream);
@@ -281,6 +282,22 @@ shk_status shk_server_get_stats(shk_server* srv, shk_server_stats* out);
  * never polled.  No other call on srv may be in progress or follow.  NULL is
  * ignored. */
 void shk_server_destroy(shk_server* srv);
+
+/* shk_int_issue_rate -- integer-issue microbenchmark of the current device.
+ * The paper has no counterpart: it measures the ceiling the leaf search's
+ * roofline is quoted against (the leaf kernels are bound by integer issue,
+ * Sec. 4's filter being a few 32-bit operations per key and seed).  One
+ * persistent launch (SMs x resident 256-thread blocks), each thread running
+ * 8 independent chains for iters iterations; best of 3 timed launches after
+ * a warm-up.
+ *   mix 0: 3-input logic + funnel shift; 1: 32-bit multiply-add; 2: both, 1:1;
+ *          3: the leaf hash and 64-bit coverage-mask update for 8 seeds x 16
+ *          keys held in registers.
+ *   *rate: lane operations per second (mix 3: key-seed evaluations per second).
+ *   *ms:   (nullable) duration of the best launch.
+ * Errors: SHK_EINVAL (mix > 3, iters = 0, rate NULL), SHK_ENOMEM, SHK_ECUDA. */
+shk_status shk_int_issue_rate(uint32_t mix, uint32_t iters, double* rate, double* ms,
+                              void* cuda_stream);
 
 /* shk_version -- format version string ("SHKRS001"). */
 const char* shk_version(void);

@@ -30,7 +30,7 @@ EXPORTS = ("shk_build", "shk_build_stats", "shk_query", "shk_serialize", "shk_de
            "shk_leaf_tune", "shk_leaf_configs", "shk_leaf_graph_replays", "shk_leaf_search_rf",
            "shk_server_create",
            "shk_server_submit", "shk_server_poll", "shk_server_wait", "shk_server_get_stats",
-           "shk_server_destroy", "shk_version", "shk_release_memory")
+           "shk_server_destroy", "shk_version", "shk_release_memory", "shk_int_issue_rate")
 
 
 class ShkError(RuntimeError):
@@ -107,6 +107,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "shk_server_destroy": (None, [vp]),
         "shk_version": (ctypes.c_char_p, []),
         "shk_release_memory": (None, []),
+        "shk_int_issue_rate": (i32, [u32, u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -284,6 +286,15 @@ def shk_release_memory() -> None:
     load_library().shk_release_memory()
 
 
+def shk_int_issue_rate(mix: int, iters: int = 4096, stream=None) -> tuple[float, float]:
+    """Integer-issue microbenchmark: (lane operations per second -- for mix 3
+    key-seed evaluations per second --, ms of the best launch)."""
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().shk_int_issue_rate(mix, iters, ctypes.byref(rate), ctypes.byref(ms),
+                                             _stream_handle(stream)))
+    return rate.value, ms.value
+
+
 def shk_free(handle) -> None:
     load_library().shk_free(handle)
 
@@ -316,17 +327,45 @@ def shk_leaf_search(leaf_keys, leaf_off, seed_start: int = 0, want_f: bool = Tru
     return seeds[:nl], (f[:nl] if f is not None else None)
 
 
+def _noalloc_check(leaf_keys, leaf_off, seeds_out, f_out):
+    """Argument checks of shk_leaf_search_noalloc, made before anything reaches
+    the library: the library writes n_leaves 8-byte words into seeds_out (and
+    f_out) on the device, so a short or narrow output would be written out of
+    bounds there."""
+    import torch
+
+    if leaf_off.dtype != torch.int32:
+        raise ValueError("leaf_off must be an int32 tensor of n_leaves + 1 offsets")
+    if leaf_off.dim() != 1 or leaf_off.numel() < 1:
+        raise ValueError("leaf_off must be a 1-D tensor of n_leaves + 1 offsets")
+    nl = leaf_off.numel() - 1
+    if leaf_keys.element_size() != 8:
+        raise ValueError("leaf_keys must hold 8-byte (64-bit) elements")
+    outs = [("seeds_out", seeds_out)] + ([("f_out", f_out)] if f_out is not None else [])
+    for name, t in outs:
+        if t.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)):
+            raise ValueError(f"{name} must be an int64 tensor")
+        if t.numel() < nl:
+            raise ValueError(f"{name} holds {t.numel()} elements, fewer than the {nl} leaves")
+    tensors = [leaf_keys, leaf_off, seeds_out] + ([f_out] if f_out is not None else [])
+    for t in tensors:
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("shk_leaf_search_noalloc takes contiguous device tensors")
+    dev = torch.cuda.current_device()
+    if any(t.device.index != dev for t in tensors):
+        raise ValueError("every tensor must be on the current CUDA device")
+    return nl
+
+
 def shk_leaf_search_noalloc(leaf_keys, leaf_off, seeds_out, f_out=None, seed_start: int = 0, stream=None):
     """shk_leaf_search for callers that cannot allocate device memory while
     they run: the caller passes the output tensors (seeds_out, and f_out or
-    None; int64 device tensors of n_leaves elements) and the library takes its
-    working memory from a fixed array in its device image, so at most 65536
-    leaves per call.  Calls that overlap on the GPU race on that array."""
+    None; int64 device tensors of at least n_leaves elements) and the library
+    takes its working memory from a fixed array in its device image, so at
+    most 65536 leaves per call.  Calls that overlap on the GPU race on that
+    array; each call synchronises its stream."""
+    nl = _noalloc_check(leaf_keys, leaf_off, seeds_out, f_out)
     lib = load_library()
-    for t in (leaf_keys, leaf_off, seeds_out) + ((f_out,) if f_out is not None else ()):
-        if not t.is_cuda or not t.is_contiguous():
-            raise ValueError("shk_leaf_search_noalloc takes contiguous device tensors")
-    nl = leaf_off.numel() - 1
     _check(lib.shk_leaf_search_noalloc(leaf_keys.data_ptr(), leaf_off.data_ptr(), nl, seed_start,
                                        seeds_out.data_ptr(), f_out.data_ptr() if f_out is not None else None,
                                        _stream_handle(stream)))

@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libshk_gpu.so")
 SOURCES = ["partition.cu", "tree.cu", "leaf.cu", "leaf_rf.cu", "encode.cu", "ribbon.cu", "query.cu",
-           "api.cu", "noalloc.cu", "server.cu"]
+           "api.cu", "noalloc.cu", "server.cu", "intpeak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -12,15 +12,15 @@
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds it (kNoAllocScratchBytes, about 1.3 MB) until the process
-// exits.  Its address is looked up once per device with
-// cudaGetSymbolAddress, on that device's first call of the entry point; make
-// that first call before any stream capture.  All calls share the one array
-// and it keeps the previous call's contents, so each call clears the parts
-// that must start at zero.  Calls whose work overlaps on the GPU (on
-// different streams, or from different host threads) race on the array and
-// must be serialised by the caller.
-#include <mutex>
-
+// exits.  Host code cannot use the symbol as a device address, so every call
+// looks the address up with cudaGetSymbolAddress on the current device (an
+// allocation-free lookup; no address is cached, so a context that was reset
+// and rebuilt is looked up afresh).  All calls share the one array and it
+// keeps the previous call's contents, so each call clears the parts that
+// must start at zero.  Calls whose work overlaps on the GPU (on different
+// streams, or from different host threads) race on the array and must be
+// serialised by the caller.  Each call reads the device error flag back and
+// synchronises its stream, so it cannot be issued inside a stream capture.
 #include "kernels.cuh"
 
 namespace shk {
@@ -39,22 +39,14 @@ constexpr size_t kNoAllocScratchBytes = kNaCountOff + 256;
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch, per device (host code may not use the
-// symbol itself as an address).
-static std::mutex g_na_mutex;
-static void* g_na_ptr[128];
-
-static shk_status noalloc_scratch(int device, uint8_t** out) {
-  if (device < 0 || device >= 128) return fail(SHK_EINVAL, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (g_na_ptr[device] == nullptr) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr)
-      return fail(SHK_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_na_ptr[device] = p;
-  }
-  *out = (uint8_t*)g_na_ptr[device];
+// Device address of g_noalloc_scratch on the current device (host code may
+// not use the symbol itself as an address).
+static shk_status noalloc_scratch(uint8_t** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr)
+    return fail(SHK_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = (uint8_t*)p;
   return SHK_OK;
 }
 
@@ -84,7 +76,7 @@ extern "C" shk_status shk_leaf_search_noalloc(const uint64_t* leaf_keys, const u
   Ctx c(st);
   SHK_TRY(init_ctx(c));
   uint8_t* scratch = nullptr;
-  SHK_TRY(noalloc_scratch(c.device, &scratch));
+  SHK_TRY(noalloc_scratch(&scratch));
   if (n_leaves == 0) return SHK_OK;
   LeafDesc* d = (LeafDesc*)scratch;
   uint32_t* state = (uint32_t*)(scratch + kNaDescBytes);

@@ -233,10 +233,13 @@ shk_status no_throw(F&& f) {
 // device (created on first use; it keeps freed memory for later calls).
 cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s);
 
-// Stream-ordered device allocations that are released together.
+// Stream-ordered device allocations that are released together.  It tracks
+// at most kCap allocations; one more fails with SHK_ENOMEM (after returning
+// the block it just took), so no allocation is ever left untracked.
 struct Arena {
+  static constexpr int kCap = 256;
   cudaStream_t stream;
-  void* ptrs[128];
+  void* ptrs[kCap];
   int n = 0;
   explicit Arena(cudaStream_t s) : stream(s) {}
   ~Arena() {
@@ -248,7 +251,11 @@ struct Arena {
     size_t bytes = count ? count * sizeof(T) : 16;
     cudaError_t e = pool_malloc(&q, bytes, stream);
     if (e != cudaSuccess) return fail(SHK_ENOMEM, std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e));
-    if (n < 128) ptrs[n++] = q;
+    if (n == kCap) {
+      cudaFreeAsync(q, stream);
+      return fail(SHK_ENOMEM, "internal: more than 256 working allocations in one call");
+    }
+    ptrs[n++] = q;
     if (zero) {
       e = cudaMemsetAsync(q, 0, bytes, stream);
       if (e != cudaSuccess) return fail(SHK_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));

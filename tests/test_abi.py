@@ -152,3 +152,29 @@ def test_oracle_and_cuda_path_share_no_code():
             text = open(path).read()
             assert not re.search(r"^\s*(import|from)\s+paper_2308_09561_gb300", text, flags=re.M), path
             assert not re.search(r'#\s*include\s*"[^"]*(csrc|shk_internal|kernels|shk\.h)', text), path
+
+
+def test_noalloc_binding_rejects_short_or_narrow_outputs_before_any_launch():
+    """shk_leaf_search_noalloc writes n_leaves 8-byte words into its outputs on
+    the device: the binding refuses outputs that are too short or too narrow,
+    and offsets of the wrong type, before the library is called (CPU tensors
+    here, so any call that got through would fail on the device check last)."""
+    import torch
+
+    import paper_2308_09561_gb300 as pkg
+
+    keys = torch.zeros(40, dtype=torch.int64)
+    off = torch.tensor([0, 10, 20, 30, 40], dtype=torch.int32)
+    with pytest.raises(ValueError, match="fewer than the 4 leaves"):
+        pkg.shk_leaf_search_noalloc(keys, off, torch.empty(3, dtype=torch.int64))
+    with pytest.raises(ValueError, match="int64"):
+        pkg.shk_leaf_search_noalloc(keys, off, torch.empty(4, dtype=torch.int32))
+    with pytest.raises(ValueError, match="f_out holds"):
+        pkg.shk_leaf_search_noalloc(keys, off, torch.empty(4, dtype=torch.int64),
+                                    f_out=torch.empty(2, dtype=torch.int64))
+    with pytest.raises(ValueError, match="int32"):
+        pkg.shk_leaf_search_noalloc(keys, off.to(torch.int64), torch.empty(4, dtype=torch.int64))
+    with pytest.raises(ValueError, match="8-byte"):
+        pkg.shk_leaf_search_noalloc(keys.to(torch.int32), off, torch.empty(4, dtype=torch.int64))
+    with pytest.raises(ValueError, match="device tensors"):
+        pkg.shk_leaf_search_noalloc(keys, off, torch.empty(4, dtype=torch.int64))
