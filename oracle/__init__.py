@@ -6,9 +6,11 @@ and the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import
 it.  It shares no code with the CUDA library: nothing here imports the
 package ``paper_2308_09561_gb300`` and the package never imports this module.
 
-Parity unpinned: the hash *values* (fingerprint, split, leaf, retrieval) -- the
-paper defines no hash function; they are pinned only through the published
-splitmix64 outputs of the mixer and statistical properties.
+The hash functions are readings (the paper defines none); each is pinned to
+something outside the oracle: the mixer to splitmix64's published outputs, the
+string fingerprint to SipHash-2-4's published test vector, and the leaf, split
+and retrieval hashes to the exact statistics of the ideal random model they
+stand for (tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 
@@ -63,6 +65,7 @@ def _load():
             "orc_mix64": (u64, [u64]),
             "orc_fp_u64": (None, [vp, u64, vp, vp]),
             "orc_fp_str": (None, [vp, vp, u64, vp, vp]),
+            "orc_siphash24": (u64, [u64, u64, vp, u64]),
             "orc_bucket": (u64, [u64, u64]),
             "orc_split_shape": (i32, [u32, u32, vp, vp]),
             "orc_split_child": (u32, [u64, u64, u32, u32, u32]),
@@ -84,6 +87,7 @@ def _load():
             "orc_rf_value": (i32, [vp, u32, u64, u64, i32, vp]),
             "orc_orient_mode": (i32, [i32, vp, u32, u64, vp]),
             "orc_ribbon_shard": (i32, [vp, vp, vp, u64, u32, vp, vp]),
+            "orc_ribbon_rows": (None, [vp, vp, u64, u32, u64, vp, vp]),
             "orc_shard_slots": (u64, [u64, u32]),
             "orc_default_shard_buckets": (u32, [u32]),
             "orc_build": (i32, [i32, vp, vp, u64, u32, u32, u32, u32, i32, i32, vp, vp]),
@@ -127,6 +131,12 @@ def fingerprints_str(data: np.ndarray, offsets) -> tuple[np.ndarray, np.ndarray]
     hi = np.empty(n, np.uint64)
     _load().orc_fp_str(_p(data), _p(offsets), n, _p(lo), _p(hi))
     return lo, hi
+
+
+def siphash24(k0: int, k1: int, msg: bytes) -> int:
+    """SipHash-2-4 of msg under the 128-bit key (k0, k1) (64-bit output)."""
+    buf = np.frombuffer(bytes(msg) + b"\0", dtype=np.uint8)
+    return int(_load().orc_siphash24(k0, k1, _p(buf), len(msg)))
 
 
 def bucket_of(hi: int, B: int) -> int:
@@ -307,6 +317,17 @@ def shard_slots(keys: int, eps_num: int = DEFAULT_EPS_NUM) -> int:
 
 def default_shard_buckets(b: int) -> int:
     return int(_load().orc_default_shard_buckets(b))
+
+
+def ribbon_rows(lo, hi, seed: int, m: int):
+    """(start, coeff) of every key's retrieval row under shard seed `seed` in
+    a shard of m slots."""
+    lo = _u64(lo)
+    hi = _u64(hi)
+    start = np.empty_like(lo)
+    coeff = np.empty_like(lo)
+    _load().orc_ribbon_rows(_p(lo), _p(hi), lo.size, seed, m, _p(start), _p(coeff))
+    return start, coeff
 
 
 def ribbon_shard(lo, hi, f, eps_num: int = DEFAULT_EPS_NUM):

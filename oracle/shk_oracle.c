@@ -26,11 +26,14 @@
  * project's frozen format readings; each function names its reading.
  *
  * Pins (tests/test_oracle_*.py): brute force over all graphs for m <= 6,
- * exact coverage probability, Fig. 2 trial counts, brute-force orientation,
- * brute-force ribbon solutions, Rice/EF round trips, bijection of every build.
- * Parity unpinned: the fingerprint, split, leaf and retrieval hash *values*
- * (the paper defines no hash function); they are pinned only through the
- * published splitmix64 outputs of the mixer and statistical properties.
+ * exact coverage probability (m up to 64), Fig. 2 trial counts (every row,
+ * n = 6 .. 40), brute-force orientation, brute-force ribbon solutions, the
+ * ribbon's success rate against random bands, Rice/EF round trips, bijection
+ * of every build.  The hash functions are readings (the paper defines none);
+ * each is pinned to something outside itself: the mixer to splitmix64's
+ * published outputs, the string fingerprint to SipHash-2-4's published test
+ * vector, and the leaf, split and retrieval hashes to the exact statistics of
+ * the ideal random model they stand for.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -106,23 +109,53 @@ void orc_fp_u64(const uint64_t* keys, uint64_t n, uint64_t* lo, uint64_t* hi) {
   }
 }
 
-/* Reading for byte-string keys: two chained lanes over 8-byte little-endian
- * words (the last one zero-padded), seeded by the length. */
+/* ------------------------------------------------------------------------ */
+/* SipHash-2-4 (Aumasson, Bernstein, "SipHash: a fast short-input PRF",      */
+/* INDOCRYPT 2012): 64-bit output under the 128-bit key (k0, k1); the message */
+/* is read as 8-byte little-endian words, the last block holding the tail     */
+/* bytes and the length mod 256 in its top byte; 2 rounds per block, 4 to     */
+/* finalize.  Written from the algorithm's description.                       */
+/* ------------------------------------------------------------------------ */
+static void sip_round(uint64_t v[4]) {
+  v[0] += v[1]; v[1] = rotl64(v[1], 13); v[1] ^= v[0]; v[0] = rotl64(v[0], 32);
+  v[2] += v[3]; v[3] = rotl64(v[3], 16); v[3] ^= v[2];
+  v[0] += v[3]; v[3] = rotl64(v[3], 21); v[3] ^= v[0];
+  v[2] += v[1]; v[1] = rotl64(v[1], 17); v[1] ^= v[2]; v[2] = rotl64(v[2], 32);
+}
+
+uint64_t orc_siphash24(uint64_t k0, uint64_t k1, const uint8_t* p, uint64_t len) {
+  uint64_t v[4] = {k0 ^ 0x736f6d6570736575ull, k1 ^ 0x646f72616e646f6dull,
+                   k0 ^ 0x6c7967656e657261ull, k1 ^ 0x7465646279746573ull};
+  const uint64_t full = len / 8;
+  for (uint64_t j = 0; j < full; j++) {
+    uint64_t w = 0;
+    for (unsigned t = 0; t < 8; t++) w |= (uint64_t)p[8 * j + t] << (8 * t);
+    v[3] ^= w;
+    sip_round(v);
+    sip_round(v);
+    v[0] ^= w;
+  }
+  uint64_t b = (len & 0xFF) << 56;
+  for (uint64_t t = 0; t < len - 8 * full; t++) b |= (uint64_t)p[8 * full + t] << (8 * t);
+  v[3] ^= b;
+  sip_round(v);
+  sip_round(v);
+  v[0] ^= b;
+  v[2] ^= 0xFF;
+  for (int r = 0; r < 4; r++) sip_round(v);
+  return v[0] ^ v[1] ^ v[2] ^ v[3];
+}
+
+/* Reading for byte-string keys: the two 64-bit halves of the fingerprint are
+ * SipHash-2-4 of the key's bytes under two fixed keys,
+ * lo = SipHash(STR_SALT_A, STR_SALT_B), hi = SipHash(STR_SALT_B, STR_SALT_A). */
 void orc_fp_str(const uint8_t* bytes, const uint64_t* offs, uint64_t n, uint64_t* lo,
                 uint64_t* hi) {
   for (uint64_t i = 0; i < n; i++) {
     const uint8_t* p = bytes + offs[i];
-    uint64_t len = offs[i + 1] - offs[i];
-    uint64_t a = orc_mix64(STR_SALT_A ^ len);
-    uint64_t b = orc_mix64(STR_SALT_B + len);
-    for (uint64_t j = 0; j < len; j += 8) {
-      uint64_t w = 0;
-      for (uint64_t t = 0; t < 8 && j + t < len; t++) w |= (uint64_t)p[j + t] << (8 * t);
-      a = orc_mix64(a ^ w);
-      b = orc_mix64(b + w);
-    }
-    hi[i] = orc_mix64(a + b);
-    lo[i] = orc_mix64(a ^ rotl64(b, 29));
+    const uint64_t len = offs[i + 1] - offs[i];
+    lo[i] = orc_siphash24(STR_SALT_A, STR_SALT_B, p, len);
+    hi[i] = orc_siphash24(STR_SALT_B, STR_SALT_A, p, len);
   }
 }
 
@@ -751,6 +784,12 @@ static void ribbon_row(uint64_t lo, uint64_t hi, uint32_t r, uint64_t m, uint64_
   uint64_t u = orc_mix64(lo ^ t);
   *start = (uint64_t)(((u128)u * (m - 63)) >> 64);
   *coeff = orc_mix64(u ^ RET_SALT2) | 1ull;
+}
+
+/* The rows of n keys under shard seed r in a shard of m slots (for tests). */
+void orc_ribbon_rows(const uint64_t* lo, const uint64_t* hi, uint64_t n, uint32_t r, uint64_t m,
+                     uint64_t* start, uint64_t* coeff) {
+  for (uint64_t i = 0; i < n; i++) ribbon_row(lo[i], hi[i], r, m, &start[i], &coeff[i]);
 }
 
 /* Gaussian elimination restricted to the band: a row is reduced by the row

@@ -8,19 +8,82 @@ namespace shk {
 // ---------------------------------------------------------------------------
 // fingerprints
 // ---------------------------------------------------------------------------
+// String fingerprint: SipHash-2-4 (Aumasson, Bernstein, INDOCRYPT 2012) of the
+// key's bytes under two fixed 128-bit keys, lo under (kStrSaltA, kStrSaltB)
+// and hi under (kStrSaltB, kStrSaltA); both instances share the word loads.
+// load(j) returns the j-th 8-byte little-endian word of the key (bytes past
+// the end may hold anything: they are masked off here).
+__device__ __forceinline__ uint64_t rotl64d(uint64_t v, int r) { return (v << r) | (v >> (64 - r)); }
+
+__device__ __forceinline__ void sip_round(uint64_t& v0, uint64_t& v1, uint64_t& v2, uint64_t& v3) {
+  v0 += v1;
+  v1 = rotl64d(v1, 13) ^ v0;
+  v0 = rotl64d(v0, 32);
+  v2 += v3;
+  v3 = rotl64d(v3, 16) ^ v2;
+  v0 += v3;
+  v3 = rotl64d(v3, 21) ^ v0;
+  v2 += v1;
+  v1 = rotl64d(v1, 17) ^ v2;
+  v2 = rotl64d(v2, 32);
+}
+
+struct Sip2 {
+  uint64_t a0, a1, a2, a3, b0, b1, b2, b3;
+  __device__ __forceinline__ Sip2() {
+    a0 = kStrSaltA ^ 0x736f6d6570736575ull;
+    a1 = kStrSaltB ^ 0x646f72616e646f6dull;
+    a2 = kStrSaltA ^ 0x6c7967656e657261ull;
+    a3 = kStrSaltB ^ 0x7465646279746573ull;
+    b0 = kStrSaltB ^ 0x736f6d6570736575ull;
+    b1 = kStrSaltA ^ 0x646f72616e646f6dull;
+    b2 = kStrSaltB ^ 0x6c7967656e657261ull;
+    b3 = kStrSaltA ^ 0x7465646279746573ull;
+  }
+  __device__ __forceinline__ void block(uint64_t w) {
+    a3 ^= w;
+    b3 ^= w;
+    sip_round(a0, a1, a2, a3);
+    sip_round(b0, b1, b2, b3);
+    sip_round(a0, a1, a2, a3);
+    sip_round(b0, b1, b2, b3);
+    a0 ^= w;
+    b0 ^= w;
+  }
+  __device__ __forceinline__ void finish(uint64_t* lo, uint64_t* hi) {
+    a2 ^= 0xFF;
+    b2 ^= 0xFF;
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      sip_round(a0, a1, a2, a3);
+      sip_round(b0, b1, b2, b3);
+    }
+    *lo = a0 ^ a1 ^ a2 ^ a3;
+    *hi = b0 ^ b1 ^ b2 ^ b3;
+  }
+};
+
+template <class Load>
+__device__ __forceinline__ void sip2_string(Load load, uint64_t len, uint64_t* lo, uint64_t* hi) {
+  Sip2 h;
+  const uint64_t full = len >> 3;
+  for (uint64_t j = 0; j < full; j++) h.block(load(j));
+  const uint32_t rem = (uint32_t)(len & 7);
+  uint64_t last = (len & 0xFF) << 56;
+  if (rem) last |= load(full) & ((1ull << (8 * rem)) - 1);
+  h.block(last);
+  h.finish(lo, hi);
+}
+
 __device__ __forceinline__ void fp_of_string(const uint8_t* p, uint64_t len, uint64_t* lo,
                                              uint64_t* hi) {
-  uint64_t a = mix64(kStrSaltA ^ len);
-  uint64_t b = mix64(kStrSaltB + len);
-  for (uint64_t j = 0; j < len; j += 8) {
+  auto load = [&](uint64_t j) {
     uint64_t w = 0;
-    const uint64_t rem = len - j < 8 ? len - j : 8;
-    for (uint64_t t = 0; t < rem; t++) w |= (uint64_t)p[j + t] << (8 * t);
-    a = mix64(a ^ w);
-    b = mix64(b + w);
-  }
-  *hi = mix64(a + b);
-  *lo = mix64(a ^ ((b << 29) | (b >> 35)));
+    const uint64_t rem = len - 8 * j < 8 ? len - 8 * j : 8;
+    for (uint64_t t = 0; t < rem; t++) w |= (uint64_t)p[8 * j + t] << (8 * t);
+    return w;
+  };
+  sip2_string(load, len, lo, hi);
 }
 
 __device__ __forceinline__ void key_fp(int kind, const void* data, const uint64_t* offs,
@@ -81,8 +144,7 @@ __device__ __forceinline__ void hist_flush(const uint32_t* hist, uint32_t* count
 // bytes (contiguous in the input) into shared memory with aligned 16-byte
 // loads -- plain byte loads only for the unaligned head and tail, so nothing
 // outside [offs[i0], offs[i0 + cnt]) is read -- and each lane then hashes its
-// key from shared memory 8 bytes at a time.  The arithmetic is that of
-// fp_of_string.  Returns false (warp-uniform) when the keys' bytes exceed the
+// key from shared memory 8 bytes at a time (the arithmetic of fp_of_string).  Returns false (warp-uniform) when the keys' bytes exceed the
 // buffer; the caller then hashes from global memory.
 constexpr uint32_t kStrBuf = 2048;  // bytes of shared memory per warp
 
@@ -114,17 +176,7 @@ __device__ bool string_fp_warp(const uint8_t* data, uint64_t s, uint64_t e, uint
   if (lane < cnt) {
     const uint64_t len = oe - o;
     const uint32_t q = (uint32_t)((uintptr_t)(data + o) - a0);
-    uint64_t a = mix64(kStrSaltA ^ len);
-    uint64_t b = mix64(kStrSaltB + len);
-    for (uint64_t j = 0; j < len; j += 8) {
-      uint64_t w = load8_smem(buf, q + (uint32_t)j);
-      const uint64_t rem = len - j;
-      if (rem < 8) w &= (1ull << (8 * rem)) - 1;
-      a = mix64(a ^ w);
-      b = mix64(b + w);
-    }
-    *hi = mix64(a + b);
-    *lo = mix64(a ^ ((b << 29) | (b >> 35)));
+    sip2_string([&](uint64_t j) { return load8_smem(buf, q + 8 * (uint32_t)j); }, len, lo, hi);
   }
   __syncwarp();
   return true;

@@ -77,7 +77,7 @@ MUTANTS = [
      lambda o: pins.test_ribbon_canonical_solution(o, 60, 3277)),
     ("retrieval: band start range one slot short",
      "*start = (uint64_t)(((u128)u * (m - 63)) >> 64);", "*start = (uint64_t)(((u128)u * (m - 64)) >> 64);",
-     lambda o: pins.test_ribbon_canonical_solution(o, 60, 3277)),
+     lambda o: pins.test_ribbon_row_start_uniform_and_coefficients_balanced(o)),
     ("retrieval: orientation bits stored inverted",
      "    uint8_t b = f[i];", "    uint8_t b = f[i] ^ 1u;",
      lambda o: build_pins.test_build_is_bijection(o, 3000, 8, 100)),
@@ -99,6 +99,28 @@ MUTANTS = [
     ("rotation fitting: first cell rotated the other way",
      "*h0 = (uint32_t)((*h0 + r) % m);", "*h0 = (uint32_t)((*h0 + m - r) % m);",
      lambda o: rf_pins.test_candidate_cells_rotation_and_partial_seed(o, 17)),
+    ("SipHash: first rotation by 12",
+     "v[1] = rotl64(v[1], 13)", "v[1] = rotl64(v[1], 12)",
+     lambda o: pins.test_siphash_published_vector(o)),
+    ("SipHash: length byte left out of the last block",
+     "uint64_t b = (len & 0xFF) << 56;", "uint64_t b = 0;",
+     lambda o: pins.test_siphash_published_vector(o)),
+    ("SipHash: tail bytes dropped",
+     "for (uint64_t t = 0; t < len - 8 * full; t++) b |=", "for (uint64_t t = 0; t < 0; t++) b |=",
+     lambda o: pins.test_siphash_published_vector(o)),
+    ("string fingerprint: both halves under the same key",
+     "hi[i] = orc_siphash24(STR_SALT_B, STR_SALT_A, p, len);", "hi[i] = orc_siphash24(STR_SALT_A, STR_SALT_B, p, len);",
+     lambda o: pins.test_string_fingerprint_is_keyed_siphash_and_sensitive(o)),
+    ("retrieval row: coefficient bit 0 not forced",
+     "*coeff = orc_mix64(u ^ RET_SALT2) | 1ull;", "*coeff = orc_mix64(u ^ RET_SALT2);",
+     lambda o: pins.test_ribbon_row_start_uniform_and_coefficients_balanced(o)),
+    ("retrieval row: band start over half the range",
+     "*start = (uint64_t)(((u128)u * (m - 63)) >> 64);", "*start = (uint64_t)(((u128)u * (m - 63)) >> 65);",
+     lambda o: pins.test_ribbon_row_start_uniform_and_coefficients_balanced(o)),
+    ("leaf hash: second cell from bits overlapping the first",
+     "uint32_t t = (uint32_t)(((uint64_t)(uint32_t)w * (m - 1)) >> 32);",
+     "uint32_t t = (uint32_t)(((uint64_t)(uint32_t)(w >> 8) * (m - 1)) >> 32);",
+     lambda o: pins.test_leaf_hash_filter_rate_matches_exact(o, 48, 4000000)),
 ]
 
 
