@@ -409,12 +409,17 @@ __device__ uint32_t find_open_leaf_rf(const uint32_t* closed, uint32_t n_leaves,
 }
 
 constexpr int kRfWarps = 8;
+// Resident blocks per SM the persistent kernel is compiled for (a register
+// budget: 65536 / (256 x this)); measured in the tuning notes.
+#ifndef SHK_RF_MIN_BLOCKS
+#define SHK_RF_MIN_BLOCKS 2
+#endif
 
 // Persistent search over all leaves with work stealing; as in plain mode the
 // work items are chunks of consecutive seeds handed out in increasing order,
 // and the minimum value is committed with atomicMin (values are v = s*m + r,
 // so seed order is value order).
-__global__ void __launch_bounds__(kRfWarps * 32)
+__global__ void __launch_bounds__(kRfWarps * 32, SHK_RF_MIN_BLOCKS)
     k_leaf_rf_persistent(const LeafDesc* __restrict__ leaves, uint32_t n_leaves,
                          const uint64_t* __restrict__ x, uint32_t passes,
                          unsigned long long* best, uint32_t* next_chunk, uint32_t* closed,
