@@ -116,6 +116,18 @@ typedef struct {
   uint64_t leaf_launches;       /* launches of the leaf-search kernel           */
   uint32_t leaf_cfg[4];         /* seeds per lane, warps per block, key unroll,  */
                                 /* passes per work item of the leaf kernel      */
+  /* Work a sequential search over the same leaves does (the roofline's      */
+  /* numerator), counted from the results:                                   */
+  uint64_t leaf_hash_evals;     /* key hash evaluations: (seed + 1) * m per      */
+                                /* plain leaf; with rotation fitting, seeds      */
+                                /* tested T = floor(v/m) + 1 and, for m > 32,    */
+                                /* |B| T + |A| ceil(T/8) (set A hashed once per  */
+                                /* 8 seeds, App. A.2), else m T                  */
+  double leaf_rf_cells;         /* rotation fitting, m > 32: (seed, missed cell) */
+                                /* steps of the bit-parallel rotation filter,    */
+                                /* 8 ceil(T/8) x E[min(cells A misses, 24 (m =   */
+                                /* 64) or 20)] given |A| (exact expectation for  */
+                                /* ideal hashing); 0 otherwise                  */
 } shk_stats;
 
 typedef struct shk_mphf shk_mphf;

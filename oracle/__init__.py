@@ -67,6 +67,7 @@ def _load():
             "orc_fp_str": (None, [vp, vp, u64, vp, vp]),
             "orc_siphash24": (u64, [u64, u64, vp, u64]),
             "orc_bucket": (u64, [u64, u64]),
+            "orc_buckets": (None, [vp, u64, u64, vp]),
             "orc_split_shape": (i32, [u32, u32, vp, vp]),
             "orc_split_child": (u32, [u64, u64, u32, u32, u32]),
             "orc_split_seed": (i32, [vp, u32, u32, vp]),
@@ -141,6 +142,14 @@ def siphash24(k0: int, k1: int, msg: bytes) -> int:
 
 def bucket_of(hi: int, B: int) -> int:
     return int(_load().orc_bucket(hi, B))
+
+
+def buckets(hi, B: int) -> np.ndarray:
+    """Bucket of every key (uint32), from the high fingerprint halves."""
+    hi = _u64(hi)
+    out = np.empty(hi.size, np.uint32)
+    _load().orc_buckets(_p(hi), hi.size, B, _p(out))
+    return out
 
 
 def split_shape(m: int, n: int):

@@ -1,9 +1,12 @@
-"""Independent reader of the serialized MPHF format, for the tests.
+"""Independent reader of the serialized MPHF format -- TEST INFRASTRUCTURE.
 
-Written from the format description (header of 16 little-endian u64 words,
-then the Rice stream, Elias-Fano of key prefixes, Elias-Fano of bit offsets,
-one seed byte per retrieval shard, and the retrieval solution, each section
-padded to whole u64 words; all bit vectors LSB-first).
+Used by the tests and by the oracle leg of the benchmark to read a serialized
+object (the GPU's or the oracle's) section by section.  Written from the
+format description, sharing no code with the C oracle or the CUDA library:
+a header of 16 little-endian u64 words, then the Rice stream, Elias-Fano of
+key prefixes, Elias-Fano of bit offsets, one seed byte per retrieval shard,
+and the retrieval solution, each section padded to whole u64 words; all bit
+vectors LSB-first.
 """
 from __future__ import annotations
 

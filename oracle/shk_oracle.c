@@ -151,6 +151,7 @@ uint64_t orc_siphash24(uint64_t k0, uint64_t k1, const uint8_t* p, uint64_t len)
  * lo = SipHash(STR_SALT_A, STR_SALT_B), hi = SipHash(STR_SALT_B, STR_SALT_A). */
 void orc_fp_str(const uint8_t* bytes, const uint64_t* offs, uint64_t n, uint64_t* lo,
                 uint64_t* hi) {
+#pragma omp parallel for schedule(static)
   for (uint64_t i = 0; i < n; i++) {
     const uint8_t* p = bytes + offs[i];
     const uint64_t len = offs[i + 1] - offs[i];
@@ -162,6 +163,12 @@ void orc_fp_str(const uint8_t* bytes, const uint64_t* offs, uint64_t n, uint64_t
 /* Bucket of a key (Sec. 2, RecSplit: keys are hashed to buckets of expected
  * size b).  Reading: B = ceil(N/b) buckets, bucket = floor(hi * B / 2^64). */
 uint64_t orc_bucket(uint64_t hi, uint64_t B) { return (uint64_t)(((u128)hi * B) >> 64); }
+
+/* The bucket of each of n keys (for tests of large builds). */
+void orc_buckets(const uint64_t* hi, uint64_t n, uint64_t B, uint32_t* out) {
+#pragma omp parallel for schedule(static)
+  for (uint64_t i = 0; i < n; i++) out[i] = (uint32_t)orc_bucket(hi[i], B);
+}
 
 /* ------------------------------------------------------------------------ */
 /* Splitting-tree shape (Sec. 2 RecSplit: the shape depends only on the      */

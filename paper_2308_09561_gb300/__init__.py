@@ -58,7 +58,8 @@ _STAT_F64 = ["ms_fingerprint", "ms_partition", "ms_split", "ms_leaf", "ms_orient
 
 class _Stats(ctypes.Structure):
     _fields_ = ([(n, ctypes.c_uint64) for n in _STAT_U64] + [(n, ctypes.c_double) for n in _STAT_F64]
-                + [("leaf_launches", ctypes.c_uint64), ("leaf_cfg", ctypes.c_uint32 * 4)])
+                + [("leaf_launches", ctypes.c_uint64), ("leaf_cfg", ctypes.c_uint32 * 4),
+                   ("leaf_hash_evals", ctypes.c_uint64), ("leaf_rf_cells", ctypes.c_double)])
 
 
 class _ReqInfo(ctypes.Structure):

@@ -326,7 +326,8 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   // a4 + a5: leaf seeds
   unsigned long long *best, *counters;
   SHK_TRY(c.arena.alloc(&best, h_L));
-  SHK_TRY(c.arena.alloc(&counters, 4, true));  // executed, sum(seed+1), sum((seed+1) m)
+  // executed, sum(seed+1), sum((seed+1) m), hash evaluations, rotation-filter steps (double)
+  SHK_TRY(c.arena.alloc(&counters, 5, true));
   if (h_L) SHK_CUDA(cudaMemsetAsync(best, 0xFF, (size_t)h_L * 8, st));
   LeafSearchArgs a{leaves, h_L, llo, 0, best, err, counters, cfg};
   uint64_t leaf_launches = 0;
@@ -348,7 +349,7 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   uint8_t* f;
   SHK_TRY(c.arena.alloc(&f, N, true));
   SHK_TRY(launch_orient(c, leaves, h_L, llo, best, codes, f, nullptr, err, rf));
-  SHK_TRY(launch_leaf_sums(c, leaves, h_L, best, counters + 1));
+  SHK_TRY(launch_leaf_sums(c, leaves, h_L, best, counters + 1, rf, llo, (double*)(counters + 4)));
   const int t5 = pt.mark();
 
   // a7 sizes: Rice bits per bucket, shard slots
@@ -367,11 +368,11 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   SHK_TRY(launch_max_shard_keys(c, K, B, S, num_shards, max_sk));
   uint64_t h_rice_bits = 0, h_rib_bits = 0;
   uint32_t h_max_sk = 0;
-  unsigned long long h_cnt[4] = {0, 0, 0, 0};
+  unsigned long long h_cnt[5] = {0, 0, 0, 0, 0};
   SHK_TRY(d2h(c, &h_rice_bits, O + B));
   SHK_TRY(d2h(c, &h_rib_bits, shard_off + num_shards));
   SHK_TRY(d2h(c, &h_max_sk, max_sk));
-  SHK_TRY(d2h(c, h_cnt, counters, 4));
+  SHK_TRY(d2h(c, h_cnt, counters, 5));
   SHK_TRY(d2h(c, &h_err, err));
   SHK_CUDA(cudaStreamSynchronize(st));
   SHK_TRY(device_errors(h_err));
@@ -437,6 +438,8 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   s.leaf_seeds_executed = h_cnt[0];
   s.leaf_seeds_min = h_cnt[1];
   s.leaf_key_evals = h_cnt[2];
+  s.leaf_hash_evals = h_cnt[3];
+  memcpy(&s.leaf_rf_cells, &h_cnt[4], sizeof(double));
   s.kernel_launches = c.launches;
   s.leaf_launches = leaf_launches;
   s.size_bits = m->words * 64;

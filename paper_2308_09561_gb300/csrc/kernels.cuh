@@ -77,8 +77,11 @@ shk_status launch_orient(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves, cons
 // rotation fitting (leaf mode 1): best[] receives v = s*m + r
 shk_status launch_leaf_rf_persistent(Ctx& c, const LeafSearchArgs& a);
 shk_status launch_leaf_rf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1);
+// sums[0..2] += sum (value + 1), sum (value + 1) m, hash evaluations of a
+// sequential search; *cells += rotation-filter steps (leaf mode 1)
 shk_status launch_leaf_sums(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves,
-                            const unsigned long long* best, unsigned long long* sums);
+                            const unsigned long long* best, unsigned long long* sums,
+                            uint32_t leaf_mode, const uint64_t* x, double* cells);
 
 // a7
 shk_status launch_rice_bits(Ctx& c, const uint64_t* codes, const uint8_t* code_k,

@@ -613,32 +613,99 @@ shk_status launch_orient(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves, cons
   return SHK_OK;
 }
 
-// Sums over leaves: sums[0] = sum (seed + 1), sums[1] = sum (seed + 1) * m.
+// Sums over leaves, counted from the results: sums[0] = sum (value + 1),
+// sums[1] = sum (value + 1) * m, sums[2] = the hash evaluations of a
+// sequential search, and (rotation fitting) *cells = its (seed, missed cell)
+// steps of the rotation filter; cbar[m * 65 + a] = E[min(cells missed by a
+// set A of a keys, K)] for m > 32 (see rf_cell_table).
 __global__ void k_leaf_sums(const LeafDesc* leaves, uint32_t n_leaves,
-                            const unsigned long long* best, unsigned long long* sums) {
-  unsigned long long a = 0, b = 0;
+                            const unsigned long long* best, unsigned long long* sums,
+                            uint32_t leaf_mode, const uint64_t* x, const double* cbar,
+                            double* cells) {
+  unsigned long long a = 0, b = 0, h = 0;
+  double cl = 0;
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n_leaves;
        l += gridDim.x * blockDim.x) {
+    const LeafDesc d = leaves[l];
     const unsigned long long s = best[l] + 1;
     a += s;
-    b += s * leaves[l].m;
+    b += s * d.m;
+    if (leaf_mode == 0 || d.m < 2) {
+      h += s * d.m;
+    } else {
+      const unsigned long long T = best[l] / d.m + 1;
+      if (d.m > 32) {
+        uint32_t na = 0;
+        for (uint32_t i = 0; i < d.m; i++) na += (mix64(x[d.key_off + i] ^ kRfSalt) >> 63) == 0;
+        const unsigned long long G = (T + 7) / 8;
+        h += (d.m - na) * T + na * G;
+        cl += 8.0 * (double)G * cbar[d.m * 65 + na];
+      } else {
+        h += T * d.m;
+      }
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(kFull, a, o);
     b += __shfl_down_sync(kFull, b, o);
+    h += __shfl_down_sync(kFull, h, o);
+    cl += __shfl_down_sync(kFull, cl, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(&sums[0], a);
     atomicAdd(&sums[1], b);
+    atomicAdd(&sums[2], h);
+    if (cells) atomicAdd(cells, cl);
+  }
+}
+
+// E[min(Z, K)] where Z = cells of an m-cell leaf missed by a keys that each
+// take two distinct uniformly random cells (K = 24 for m = 64, 20 otherwise:
+// the missed cells the rotation filter intersects without branches), for
+// m = 33..64 and a = 0..m; exact, by the distribution of covered cells.
+static void rf_cell_table(double* t) {
+  for (int i = 0; i < 65 * 65; i++) t[i] = 0;
+  for (int m = 33; m <= 64; m++) {
+    const int K = m == 64 ? 24 : 20;
+    double p[65] = {0}, q[65];
+    p[0] = 1;
+    const double pairs = (double)m * (m - 1);
+    for (int a = 0; a <= m; a++) {
+      double e = 0;
+      for (int k = 0; k <= m; k++) e += p[k] * (double)(m - k < K ? m - k : K);
+      t[m * 65 + a] = e;
+      for (int k = 0; k <= m; k++) q[k] = 0;
+      for (int k = 0; k <= m; k++) {
+        if (p[k] == 0) continue;
+        const double two = (double)(m - k) * (m - k - 1) / pairs;
+        const double one = 2.0 * k * (m - k) / pairs;
+        const double zero = (double)k * (k - 1) / pairs;
+        q[k] += p[k] * zero;
+        if (k + 1 <= m) q[k + 1] += p[k] * one;
+        if (k + 2 <= m) q[k + 2] += p[k] * two;
+      }
+      for (int k = 0; k <= m; k++) p[k] = q[k];
+    }
   }
 }
 
 shk_status launch_leaf_sums(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves,
-                            const unsigned long long* best, unsigned long long* sums) {
+                            const unsigned long long* best, unsigned long long* sums,
+                            uint32_t leaf_mode, const uint64_t* x, double* cells) {
   if (n_leaves == 0) return SHK_OK;
+  double* cbar = nullptr;
+  if (leaf_mode) {
+    double host[65 * 65];
+    rf_cell_table(host);
+    SHK_TRY(c.arena.alloc(&cbar, 65 * 65));
+    SHK_CUDA(cudaMemcpyAsync(cbar, host, sizeof host, cudaMemcpyHostToDevice, c.stream));
+    // the host table must outlive the copy
+    SHK_CUDA(cudaStreamSynchronize(c.stream));
+  }
   uint32_t blocks = (n_leaves + 255) / 256;
   if (blocks > 1024) blocks = 1024;
-  k_leaf_sums<<<blocks, 256, 0, c.stream>>>(leaves, n_leaves, best, sums);
+  k_leaf_sums<<<blocks, 256, 0, c.stream>>>(leaves, n_leaves, best, sums, leaf_mode, x, cbar,
+                                            leaf_mode ? cells : nullptr);
   c.launches++;
   SHK_CUDA(cudaGetLastError());
   return SHK_OK;

@@ -100,3 +100,30 @@ def ascii_strings(count: int, seed: int, min_len: int = 10, max_len: int = 50,
         raw = splitmix64_stream(seed, n, start=count + 1 + a)
         data[a:a + n] = (1 + (raw % np.uint64(127))).astype(np.uint8)
     return data, offs
+
+
+def ascii_strings_torch(count: int, seed: int, min_len: int = 10, max_len: int = 50,
+                        device="cuda", chunk: int = 1 << 27):
+    """``ascii_strings`` computed on ``device`` with torch integer arithmetic:
+    the same (bytes, offsets) bit for bit, as a uint8 and an int64 tensor.
+    Lengths take the top 53 bits of the stream as a double exactly as numpy
+    does; a byte is 1 + (r mod 127) with r mod 127 taken from the 32-bit
+    halves of r (2^32 = 16 mod 127, since 2^7 = 1 mod 127)."""
+    import torch
+
+    span = max_len - min_len + 1
+    z = splitmix64_stream_torch(seed, count, start=1, device=device)
+    u = ((z >> 11) & ((1 << 53) - 1)).to(torch.float64) * (2.0**-53)
+    lens = min_len + torch.floor(u * span).to(torch.int64)
+    del z, u
+    offs = torch.zeros(count + 1, dtype=torch.int64, device=device)
+    torch.cumsum(lens, 0, out=offs[1:])
+    total = int(offs[-1])
+    data = torch.empty(total, dtype=torch.uint8, device=device)
+    for a in range(0, total, chunk):
+        n = min(chunk, total - a)
+        r = splitmix64_stream_torch(seed, n, start=count + 1 + a, device=device)
+        mod = (((r >> 32) & 0xFFFFFFFF) * 16 + (r & 0xFFFFFFFF)) % 127
+        data[a:a + n] = (1 + mod).to(torch.uint8)
+        del r, mod
+    return data, offs

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import shk_inputs as inp
-from blobfmt import Blob
+from oracle.blobfmt import Blob
 
 pytestmark = pytest.mark.gpu
 

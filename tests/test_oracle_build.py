@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import shk_inputs as inp
-from blobfmt import Blob
+from oracle.blobfmt import Blob
 
 
 def _check_bijection(orc, blob, lo, hi):

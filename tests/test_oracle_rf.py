@@ -102,7 +102,7 @@ def test_rf_candidates_match_plain_trials(orc):
 
 @pytest.mark.parametrize("N,n,b", [(5000, 24, 800), (3000, 36, 1000), (777, 40, 2000), (2, 2, 2), (129, 16, 16)])
 def test_rf_build_is_bijection(orc, N, n, b):
-    from blobfmt import Blob
+    from oracle.blobfmt import Blob
 
     keys = inp.distinct_u64(N, 300 + N)
     blob = orc.build_mphf(keys, n=n, b=b, leaf_mode=1)
