@@ -364,16 +364,35 @@ void orc_rf_cells(uint64_t x, uint64_t v, uint32_t m, uint32_t* h0, uint32_t* h1
   }
 }
 
+/* The rotation-fitting search in the paper's order (Sec. 4, Rotation
+ * Fitting): the keys are split into the two sets once; for each seed s both
+ * sets are hashed (set A with its partial seed, App. A.2); then for each
+ * rotation r = 0 .. m-1 the cells of set B are moved by r and the candidate
+ * v = s*m + r is tested (filter, then pseudoforest).  Candidates are visited
+ * in increasing v, so the first that passes is the minimum; the cells of
+ * every candidate are those orc_rf_cells gives. */
 int orc_rf_value(const uint64_t* x, uint32_t m, uint64_t start, uint64_t cap, int use_filter,
                  uint64_t* v_out) {
-  uint32_t h0[ORC_MAX_LEAF], h1[ORC_MAX_LEAF];
+  uint32_t a0[ORC_MAX_LEAF], a1[ORC_MAX_LEAF], h0[ORC_MAX_LEAF], h1[ORC_MAX_LEAF];
+  int in_b[ORC_MAX_LEAF];
   if (m < 2 || m > ORC_MAX_LEAF) return ORC_EINVAL;
-  for (uint64_t v = start; v < cap; v++) {
-    for (uint32_t i = 0; i < m; i++) orc_rf_cells(x[i], v, m, &h0[i], &h1[i]);
-    if (use_filter && !orc_covers_all(h0, h1, m)) continue;
-    if (orc_is_pseudoforest(h0, h1, m)) {
-      *v_out = v;
-      return ORC_OK;
+  for (uint32_t i = 0; i < m; i++) in_b[i] = orc_rf_set(x[i]);
+  for (uint64_t s = start / m; s * m < cap; s++) {
+    const uint64_t sa = m > 32 ? s - s % RF_PARTIAL_K : s;
+    for (uint32_t i = 0; i < m; i++) orc_leaf_hash(x[i], in_b[i] ? s : sa, m, &a0[i], &a1[i]);
+    for (uint32_t r = 0; r < m; r++) {
+      const uint64_t v = s * m + r;
+      if (v < start) continue;
+      if (v >= cap) break;
+      for (uint32_t i = 0; i < m; i++) {  /* B's cells moved by r, mod m */
+        h0[i] = in_b[i] ? (a0[i] + r >= m ? a0[i] + r - m : a0[i] + r) : a0[i];
+        h1[i] = in_b[i] ? (a1[i] + r >= m ? a1[i] + r - m : a1[i] + r) : a1[i];
+      }
+      if (use_filter && !orc_covers_all(h0, h1, m)) continue;
+      if (orc_is_pseudoforest(h0, h1, m)) {
+        *v_out = v;
+        return ORC_OK;
+      }
     }
   }
   return ORC_ESEEDCAP;
