@@ -1,11 +1,13 @@
-"""Benchmark: MPHF builds of 10^6 uniform 64-bit keys (splitmix64 stream seed 2),
-leaf size 48, bucket size 2000, on one GB300 per rank.
+"""Benchmark: MPHF construction of 10^8 random strings (lengths 10..50, bytes
+1..127, splitmix64 stream seed 4), leaf size 64, bucket size 2000, rotation
+fitting with partial hash calculation, retrieval overhead 1.5 %, on one GB300
+per rank.
 
-A step is one whole build (fingerprints, bucket partition, splitting trees,
-leaf seed search, orientation, Golomb-Rice/Elias-Fano encoding, retrieval
-solve) from keys resident in HBM to the encoded MPHF in HBM.  Prints one JSON
-line (rank 0).  Ranks build independent key sets (weak scaling, no collective
-on the data path).
+A step is one whole build (string fingerprints, bucket partition, splitting
+trees, leaf search, orientation, Golomb-Rice/Elias-Fano encoding, retrieval
+solve) from the strings resident in HBM to the encoded MPHF in HBM.  Prints one
+JSON line (rank 0) with the 10^6-key, leaf-48 build as a sub-record.  Ranks
+build independent key sets (weak scaling, no collective on the data path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -24,16 +26,25 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# headline workload: 10^8 strings, leaf 64, bucket 2000, rotation fitting
+STR_KEYS, STR_LEAF, STR_BUCKET, STR_SEED, STR_EPS = 100_000_000, 64, 2000, 4, 983
+WORKLOAD = "mphf_build_1e8_strings_leaf64_bucket2000"
+METRIC = ("MPHF build keys/s (10^8 random strings, leaf 64, bucket 2000, rotation fitting), "
+          "leaf seeds tested/s, % integer-issue roofline")
+# sub-record workload: 10^6 distinct u64 keys, leaf 48, bucket 2000
 N_KEYS, LEAF, BUCKET, KEY_SEED = 1_000_000, 48, 2000, 2
-WORKLOAD = "mphf_build_1M_u64_keys_leaf48_bucket2000"
-METRIC = "MPHF build keys/s (1M u64 keys, leaf 48, bucket 2000), leaf seeds tested/s, % integer-issue roofline"
 # integer lane-operations of one key-seed evaluation of the leaf hash + filter:
 # xor 1, multiply-add 1, widening multiply by m 1, multiply-high by m-1 1,
 # h1 adjust 2 (compare, add), two candidate bits into the mask: 8 when the mask
 # is two 32-bit words (2 subtracts, 4 shifts, 2 ors; m > 32), 3 for m <= 32
 OPS_PER_EVAL_WIDE = 14
-LEAF_TRAFFIC_PER_LEAF = 920_576 / 2_100  # DRAM bytes per leaf of the leaf kernel, measured with ncu
 OPS_PER_EVAL_NARROW = 9
+# rotation fitting: one (seed, missed cell) step of the bit-parallel rotation
+# filter = rotate the reflected 64-bit B mask (two 32-bit funnel shifts) and
+# AND it into the seed's rotation set (one op, a three-input AND taking two
+# cells per word)
+OPS_PER_RF_CELL = 3
+LEAF_TRAFFIC_PER_LEAF = 920_576 / 2_100  # DRAM bytes per leaf of the plain leaf kernel, ncu
 
 
 def _peaks():
@@ -124,162 +135,147 @@ def max_over_ranks(seconds: float, dist, device) -> float:
     return float(t.item())
 
 
-def _cpu_baseline(sample_keys: int, reps: int = 1, single_keys: int = 0):
-    """The oracle as it stands on the host cores, on the first sample_keys keys
-    of the same stream (same leaf and bucket size).  With single_keys > 0 it is
-    also timed on one thread over the first single_keys keys."""
+def _oracle_leaf_step(step: int, leaves: int = 16):
+    """One bounded step of the oracle on the headline workload's leaves: the
+    strings [2000 step, 2000 (step + 1)) of the same stream taken as one
+    bucket (leaf 64), its splitting tree by the oracle, then the oracle's
+    rotation-fitting leaf search (OpenMP over leaves) on `leaves` of its leaves
+    drawn at random.  Returns (keys searched, seconds of the leaf search,
+    threads).  The leaf search is the oracle's dominant cost at leaf size 64
+    (splits, encoding and retrieval are well under 1 % of it)."""
     import oracle
-
-    oracle.build()
     import shk_inputs
 
-    keys = shk_inputs.distinct_u64(max(sample_keys, single_keys), KEY_SEED)
-    cores = os.cpu_count() or 1
+    oracle.build()
+    data, offs = shk_inputs.ascii_strings(STR_BUCKET * (step + 1), STR_SEED)
+    a = STR_BUCKET * step
+    sub = data[int(offs[a]):int(offs[-1])]
+    so = offs[a:] - offs[a]
+    lo, hi = oracle.fingerprints_str(sub, so)
+    order = np.lexsort((lo, hi))
+    _, _, llo, _, loff, lm = oracle.bucket_splits(lo[order], hi[order], STR_LEAF)
+    pick = np.sort(np.random.default_rng(1000 + step).choice(lm.size, min(leaves, lm.size), replace=False))
+    packed = np.concatenate([llo[loff[j]:loff[j] + lm[j]] for j in pick])
+    po = np.zeros(pick.size + 1, np.uint32)
+    po[1:] = np.cumsum(lm[pick])
+    threads = min(os.cpu_count() or 1, int(pick.size))
     t = time.perf_counter()
-    for _ in range(reps):
-        oracle.build_mphf(keys[:sample_keys], n=LEAF, b=BUCKET, nthreads=cores)
-    dt = time.perf_counter() - t
-    out = {"value": sample_keys * reps / dt, "unit": "keys/s", "cores": cores, "kind": "oracle",
-           "sample": f"first {sample_keys} keys of the same stream ({(sample_keys + BUCKET - 1) // BUCKET} buckets), "
-                     f"leaf 48, bucket 2000, OpenMP over buckets, {reps} build(s), {dt:.1f} s"}
-    if single_keys:
-        t = time.perf_counter()
-        oracle.build_mphf(keys[:single_keys], n=LEAF, b=BUCKET, nthreads=1)
-        dt1 = time.perf_counter() - t
-        out["single_thread"] = {"value": single_keys / dt1, "unit": "keys/s",
-                                "sample": f"first {single_keys} keys, one thread, {dt1:.1f} s"}
-    return out
+    oracle.leaf_search_batch(packed, po, 0, nthreads=threads, rf=True)
+    return int(po[-1]), time.perf_counter() - t, threads
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    headline workload per step (see _oracle_leaf_step)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    sample = args.ref_sample_keys
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; warm-up steps would only add minutes
-    t = time.perf_counter()
-    base = None
-    for _ in range(args.steps):
-        base = _cpu_baseline(sample)
-    dt = time.perf_counter() - t
-    value = sample * args.steps / dt
-    base["value"] = value
+    keys = secs = 0.0
+    threads = 1
+    t0 = time.perf_counter()
+    for step in range(args.steps):
+        k, dt, threads = _oracle_leaf_step(step, args.ref_leaves)
+        keys += k
+        secs += dt
+    wall = time.perf_counter() - t0
+    value = keys / secs
     line = {"metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "keys": N_KEYS, "leaf_size": LEAF, "bucket_size": BUCKET,
-                       "sample_keys": sample},
-            "cpu_baseline": base,
+            "config": {"workload": WORKLOAD, "keys": STR_KEYS, "leaf_size": STR_LEAF, "bucket_size": STR_BUCKET,
+                       "leaf_mode": "rotation fitting", "eps_num": STR_EPS,
+                       "sample": f"{args.ref_leaves} leaves per step"},
+            "cpu_baseline": {"value": value, "unit": "keys/s", "cores": threads, "kind": "oracle",
+                             "sample": f"per step: the rotation-fitting leaf search of {args.ref_leaves} leaves of "
+                                       f"a 2,000-string bucket of the same stream (step i: strings 2000 i .. "
+                                       f"2000 (i+1) - 1), OpenMP over leaves; keys/s = leaf keys / search time; "
+                                       f"{args.steps} steps, {wall:.0f} s wall"},
             "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_ours(args):
+def _int_issue(pkg):
+    """Integer-issue microbenchmark (the library's shk_int_issue_rate)."""
+    out = {}
+    for mix, name in ((0, "alu_lop3_shf"), (1, "fma_imad"), (2, "imad_plus_lop3"), (3, "leaf_hash_evals")):
+        rate, ms = pkg.shk_int_issue_rate(mix, 4096 if mix < 3 else 256)
+        out[name] = rate / (1e12 if mix < 3 else 1.0)
+    out["unit"] = "T lane-ops/s (leaf_hash_evals: key-seed evaluations/s)"
+    return out
+
+
+def u64_subrecord(pkg, args, flush, stream, peak_tops, cfg):
+    """The 10^6 distinct u64 keys (stream seed 2), leaf 48, bucket 2000 build:
+    plain leaves (with the plain leaf kernel's roofline), the same keys with
+    rotation fitting, the leaf schedules compared, and queries."""
     import torch
 
-    global N_KEYS
-    N_KEYS = args.keys or N_KEYS
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    import paper_2308_09561_gb300 as pkg
     import shk_inputs
 
-    pkg.load_library()
-    keys = shk_inputs.distinct_u64(N_KEYS, rank_key_seed(rank))
+    keys = shk_inputs.distinct_u64(N_KEYS, KEY_SEED)
     dkeys = torch.from_numpy(keys.view(np.int64)).cuda()
-    host_keys = torch.from_numpy(keys.view(np.int64)).pin_memory()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # 256 MB > L2
-    stream = torch.cuda.current_stream()
-
-    cfg = {}
-    if args.leaf_cfg:
-        u, w, r = (int(v) for v in args.leaf_cfg.split(","))
-        cfg = {"seeds_per_lane": u, "warps_per_block": w, "key_unroll": r, "chunk_passes": 8}
-
-    def step(profile=True):
-        m = pkg.shk_build(dkeys, LEAF, BUCKET, profile=profile, **cfg)
-        st = m.stats()
-        m.close()
-        return st
-
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize()
-    stats = []
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        wall0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.fill_(i)
-            ev[i][0].record(stream)
-            stats.append(step())
-            ev[i][1].record(stream)
+    for _ in range(2):
+        pkg.shk_build(dkeys, LEAF, BUCKET, **cfg).close()
+    stats, ms = [], []
+    for i in range(3):
+        flush.fill_(i)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m = pkg.shk_build(dkeys, LEAF, BUCKET, profile=True, **cfg)
+        b.record(stream)
         torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_sum = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
-    value = N_KEYS * ws * args.steps / t_sum
-
-    # end to end through the public API: pinned host keys in, serialized MPHF out
-    e2e_ms = []
-    blob_bytes = 0
-    for i in range(max(1, min(args.steps, 3))):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        m = pkg.shk_build(host_keys, LEAF, BUCKET, **cfg)
-        blob = m.serialize()
-        e2e_ms.append(1e3 * (time.perf_counter() - t))
-        blob_bytes = len(blob)
+        ms.append(a.elapsed_time(b))
+        stats.append(m.stats())
+        blob_bytes = len(m.serialize())
         m.close()
-    e2e_value = N_KEYS * ws / (np.mean(e2e_ms) / 1e3)
-
-    leaf_ms = np.mean([s["ms_leaf"] for s in stats])
-    seeds_min = stats[-1]["leaf_seeds_min"]
+    leaf_ms = float(np.mean([s["ms_leaf"] for s in stats]))
     evals = stats[-1]["leaf_key_evals"]
-    peaks = _peaks()
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tops = sms * 4 * 32 * sm_max_mhz * 1e6 / 1e12
-    achieved_tops = evals * OPS_PER_EVAL_WIDE / (leaf_ms / 1e3) / 1e12
-    clocks = clk.summary()
-    # the plain form: one leaf-search launch per bucket, one warp per leaf, on a
-    # prefix of the same keys (the whole workload with --compare-per-bucket)
-    cmp_keys = N_KEYS if args.compare_per_bucket else min(N_KEYS, 100_000)
-    ck = dkeys[:cmp_keys]
-    t_cmp = {}
-    for name, sched in (("persistent", pkg.SHK_SCHED_PERSISTENT), ("per_bucket", pkg.SHK_SCHED_PER_BUCKET)):
-        m = pkg.shk_build(ck, LEAF, BUCKET, sched=sched, profile=True, **cfg)
-        st = m.stats()
-        t_cmp[name] = st
-        m.close()
-    # rotation fitting with partial hash calculation (leaf mode 1) on the same keys
-    rf_stats = []
+    ach = evals * OPS_PER_EVAL_WIDE / (leaf_ms / 1e3) / 1e12
+    rec = {"workload": "mphf_build_1M_u64_keys_leaf48_bucket2000", "keys": N_KEYS,
+           "keys_per_s": N_KEYS / (float(np.mean(ms)) / 1e3), "ms_per_build": float(np.mean(ms)),
+           "bits_per_key": 8 * blob_bytes / N_KEYS,
+           "leaf_seeds_per_s": stats[-1]["leaf_seeds_min"] / (leaf_ms / 1e3),
+           "key_seed_evals_per_s": evals / (leaf_ms / 1e3),
+           "leaf_kernel_cfg": stats[-1]["leaf_cfg"],
+           "phase_ms": {k: float(np.mean([s[k] for s in stats])) for k in
+                        ("ms_fingerprint", "ms_partition", "ms_split", "ms_leaf", "ms_orient", "ms_encode",
+                         "ms_ribbon", "ms_total")},
+           "roofline": {"bound": "alu", "kernel": "k_leaf_persistent", "achieved": ach, "peak": peak_tops,
+                        "unit": "T int-lane-ops/s", "frac": ach / peak_tops,
+                        "traffic": LEAF_TRAFFIC_PER_LEAF * stats[-1]["n_leaves"],
+                        "traffic_note": "scaled by leaves from an ncu capture of the 10^5-key build",
+                        "ops_per_launch": evals * OPS_PER_EVAL_WIDE}}
+    # rotation fitting with partial hash calculation on the same keys
+    rf = []
     for _ in range(3):
         m = pkg.shk_build(dkeys, LEAF, BUCKET, leaf_mode=pkg.SHK_LEAF_ROTATION, profile=True)
-        rf_stats.append(m.stats())
-        rf_bytes = len(m.serialize())
+        rf.append(m.stats())
         m.close()
-    rf_ms = float(np.median([s["ms_total"] for s in rf_stats]))
-    rotation = {"keys_per_s": N_KEYS / (rf_ms / 1e3), "ms_total": rf_ms,
-                "ms_leaf": float(np.median([s["ms_leaf"] for s in rf_stats])),
-                "leaf_candidates_per_s": rf_stats[-1]["leaf_seeds_min"] / (rf_stats[-1]["ms_leaf"] / 1e3),
-                "bits_per_key": 8 * rf_bytes / N_KEYS,
-                "note": "candidates = sum over leaves of (v+1), v = seed*m + rotation"}
-    # queries: every key of the workload, device in and out, L2 flushed before each pass
+    rf_ms = float(np.median([s["ms_total"] for s in rf]))
+    rec["rotation_fitting"] = {"keys_per_s": N_KEYS / (rf_ms / 1e3), "ms_total": rf_ms,
+                               "ms_leaf": float(np.median([s["ms_leaf"] for s in rf]))}
+    # leaf schedules: the persistent work-stealing launch, one launch over all
+    # leaves with one warp per leaf (no work sharing), and one launch per
+    # bucket; the per-bucket form on 10^5 keys (the whole set with
+    # --compare-per-bucket), the others on all 10^6
+    sched = {}
+    for name, sc, nk in (("persistent", pkg.SHK_SCHED_PERSISTENT, N_KEYS),
+                         ("single_launch_one_warp_per_leaf", pkg.SHK_SCHED_SINGLE_LAUNCH, N_KEYS),
+                         ("persistent_100k", pkg.SHK_SCHED_PERSISTENT, 100_000),
+                         ("per_bucket_100k", pkg.SHK_SCHED_PER_BUCKET, N_KEYS if args.compare_per_bucket
+                          else 100_000)):
+        m = pkg.shk_build(dkeys[:nk], LEAF, BUCKET, sched=sc, profile=True, **cfg)
+        st = m.stats()
+        m.close()
+        sched[name] = {"keys": nk, "ms_leaf": st["ms_leaf"], "leaf_launches": st["leaf_launches"]}
+    sched["speedup_persistent_vs_single_launch"] = (sched["single_launch_one_warp_per_leaf"]["ms_leaf"]
+                                                    / sched["persistent"]["ms_leaf"])
+    sched["speedup_persistent_vs_per_bucket"] = (sched["per_bucket_100k"]["ms_leaf"]
+                                                 / sched["persistent_100k"]["ms_leaf"])
+    rec["leaf_schedules"] = sched
+    # queries: every key, device in and out, L2 flushed before each pass
     mq = pkg.shk_build(dkeys, LEAF, BUCKET, **cfg)
     mq.query(dkeys)
     q_ms = []
@@ -292,50 +288,180 @@ def run_ours(args):
         torch.cuda.synchronize()
         q_ms.append(a.elapsed_time(b))
     mq.close()
-    query = {"keys_per_s": N_KEYS / (float(np.median(q_ms)) / 1e3), "ms": float(np.median(q_ms)),
-             "note": "shk_query over all keys (fingerprint, bucket, tree descent through the query "
-                     "index built by the first query, retrieval parity)"}
-    per_bucket = {"keys": cmp_keys, "persistent_ms_leaf": t_cmp["persistent"]["ms_leaf"],
-                  "per_bucket_ms_leaf": t_cmp["per_bucket"]["ms_leaf"],
-                  "per_bucket_leaf_launches": t_cmp["per_bucket"]["leaf_launches"],
-                  "speedup_leaf": t_cmp["per_bucket"]["ms_leaf"] / t_cmp["persistent"]["ms_leaf"],
-                  "speedup_build": t_cmp["per_bucket"]["ms_total"] / t_cmp["persistent"]["ms_total"]}
+    rec["query_keys_per_s"] = N_KEYS / (float(np.median(q_ms)) / 1e3)
+    return rec, int(sum(s["kernel_launches"] for s in stats))
+
+
+def run_ours(args):
+    """The headline: builds of the 10^8-string workload (see the module
+    docstring), then its checks, the end-to-end number, sub-records and the
+    oracle leg."""
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import paper_2308_09561_gb300 as pkg
+    import shk_inputs
+
+    pkg.load_library()
+    count = args.keys or STR_KEYS
+    t = time.perf_counter()
+    ddata, doffs = shk_inputs.ascii_strings_torch(count, STR_SEED + 1000 * rank, device="cuda")
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t
+    hdata = ddata.cpu().pin_memory()
+    hoffs = doffs.cpu().pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    mode = pkg.SHK_LEAF_ROTATION if args.leaf_mode == "rf" else pkg.SHK_LEAF_PLAIN
+    opts = dict(kind=pkg.SHK_KEYS_STR, leaf_mode=mode, eps_num=args.eps_num)
+
+    def build(data, offs, profile=True):
+        return pkg.shk_build(data, STR_LEAF, STR_BUCKET, str_offsets=offs, profile=profile, **opts)
+
+    for _ in range(max(args.warmup, 0)):
+        build(ddata, doffs).close()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats, last = [], None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(i)
+            ev[i][0].record(stream)
+            m = build(ddata, doffs)
+            ev[i][1].record(stream)
+            stats.append(m.stats())
+            if last is not None:
+                last.close()
+            last = m
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_sum = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
+    value = count * ws * args.steps / t_sum
+    clocks = clk.summary()
+    st = stats[-1]
+
+    # every key ranks bijectively (the last timed build)
+    blob = last.serialize()
+    torch.cuda.synchronize()
+    tq = time.perf_counter()
+    ranks = last.query(ddata, kind=pkg.SHK_KEYS_STR, str_offsets=doffs)
+    torch.cuda.synchronize()
+    query_s = time.perf_counter() - tq
+    srt, _ = torch.sort(ranks)
+    bijection = bool(torch.equal(srt, torch.arange(count, device="cuda", dtype=torch.int64)))
+    del srt, ranks
+    last.close()
+
+    # end to end through the public API: pinned host strings in, serialized MPHF out
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    m = build(hdata, hoffs, profile=False)
+    e2e_blob = m.serialize()
+    e2e_s = time.perf_counter() - t
+    m.close()
+    e2e_same = e2e_blob == blob
+
+    # roofline of the rotation-fitting leaf kernel (or the plain one)
+    peaks = _peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tops = sms * 4 * 32 * sm_max_mhz * 1e6 / 1e12
+    leaf_ms = float(np.mean([s["ms_leaf"] for s in stats]))
+    if mode == pkg.SHK_LEAF_ROTATION:
+        ops = st["leaf_hash_evals"] * OPS_PER_EVAL_WIDE + st["leaf_rf_cells"] * OPS_PER_RF_CELL
+        kernel = "k_leaf_rf_persistent"
+        ops_note = (f"{OPS_PER_EVAL_WIDE} per key hash evaluation (a sequential search's: |B| T + |A| ceil(T/8) "
+                    f"per leaf, T = seeds tested) + {OPS_PER_RF_CELL} per (seed, missed cell) step of the "
+                    f"bit-parallel rotation filter (expected steps given |A|)")
+    else:
+        ops = st["leaf_key_evals"] * OPS_PER_EVAL_WIDE
+        kernel = "k_leaf_persistent"
+        ops_note = f"{OPS_PER_EVAL_WIDE} per key-seed evaluation, sum over leaves of (seed + 1) m"
+    achieved = ops / (leaf_ms / 1e3) / 1e12
+    ints = _int_issue(pkg)
+    roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_tops,
+                "unit": "T int-lane-ops/s", "frac": achieved / peak_tops, "traffic": None,
+                "traffic_note": "no DRAM traffic to speak of: each leaf's keys are read once into "
+                                "shared memory (ncu capture summarised in profiles/)",
+                "ops_per_launch": ops, "ops_note": ops_note,
+                "peak_note": f"{sms} SMs x 4 schedulers x 32 lanes x {sm_max_mhz:.0f} MHz (max SM clock); "
+                             f"measured achievable on this GPU (1:1 multiply-add + logic): "
+                             f"{ints['imad_plus_lop3']:.1f}",
+                "frac_of_measured_achievable": achieved / ints["imad_plus_lop3"]}
+    cfg = {}
+    if args.leaf_cfg:
+        u, w, r = (int(v) for v in args.leaf_cfg.split(","))
+        cfg = {"seeds_per_lane": u, "warps_per_block": w, "key_unroll": r, "chunk_passes": 8}
+    u64rec, u64_launches = ({}, 0) if args.no_subrecords else u64_subrecord(pkg, args, flush, stream, peak_tops, cfg)
+    part_bytes = int(hdata.numel()) + 8 * (count + 1) + 16 * count + 32 * count
+    part_ms = float(np.mean([s["ms_fingerprint"] + s["ms_partition"] for s in stats]))
     line = {
         "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_sum / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "keys": N_KEYS, "leaf_size": LEAF, "bucket_size": BUCKET,
-                   "key_stream_seed": KEY_SEED, "schedule": "persistent",
-                   "l2": "256 MB buffer written between timed steps (flush), outside the step events",
+        "config": {"workload": WORKLOAD, "keys": count, "string_bytes": int(hdata.numel()),
+                   "leaf_size": STR_LEAF, "bucket_size": STR_BUCKET, "leaf_mode": args.leaf_mode,
+                   "eps_num": args.eps_num, "key_stream_seed": STR_SEED, "schedule": "persistent",
+                   "l2": "inputs larger than L2 (string bytes + offsets); also 256 MB written between timed "
+                         "steps, outside the step events",
                    "parallelism": f"replicas x{ws}"},
-        "leaf_seeds_per_s": seeds_min / (leaf_ms / 1e3),
-        "leaf_seeds_per_s_build": seeds_min * ws * args.steps / t_sum,
-        "key_seed_evals_per_s": evals / (leaf_ms / 1e3),
-        "bits_per_key": 8 * blob_bytes / N_KEYS,
+        "bits_per_key": 8 * len(blob) / count,
+        "bijection_all_keys": bijection,
+        "leaf_seeds_per_s": st["leaf_seeds_tested"] / (leaf_ms / 1e3),
+        "leaf_candidates_per_s": st["leaf_seeds_min"] / (leaf_ms / 1e3),
+        "leaf_hash_evals_per_s": st["leaf_hash_evals"] / (leaf_ms / 1e3),
+        "leaf_note": "seeds tested = sum over leaves of floor(v/m) + 1 (rotation fitting; seed + 1 plain); "
+                     "candidates = sum of (v + 1), v = seed m + rotation",
         "phase_ms": {k: float(np.mean([s[k] for s in stats])) for k in
                      ("ms_fingerprint", "ms_partition", "ms_split", "ms_leaf", "ms_orient", "ms_encode",
                       "ms_ribbon", "ms_total")},
-        "roofline": {"bound": "alu", "kernel": "k_leaf_persistent", "achieved": achieved_tops,
-                     "peak": peak_tops, "unit": "T int-lane-ops/s", "frac": achieved_tops / peak_tops,
-                     # ncu dram read + write of k_leaf_persistent<4,8,4> on the 10^5-key build
-                     # (920.6 KB over 2,100 leaves), scaled by the leaves of this launch
-                     "traffic": LEAF_TRAFFIC_PER_LEAF * stats[-1]["n_leaves"],
-                     "traffic_note": "scaled by leaves from an ncu capture of the 10^5-key build",
-                     "ops_per_launch": evals * OPS_PER_EVAL_WIDE,
-                     "peak_note": f"{sms} SMs x 4 schedulers x 32 lanes x {sm_max_mhz:.0f} MHz (max SM clock)"},
-        "e2e": {"value": e2e_value, "unit": "keys/s", "h2d_bytes_per_step": N_KEYS * 8,
-                "d2h_bytes_per_step": blob_bytes},
+        "partition_gbs": part_bytes / (part_ms / 1e3) / 1e9,
+        "roofline": roofline,
+        "int_issue_microbench": ints,
+        "e2e": {"value": count * ws / e2e_s, "unit": "keys/s", "h2d_bytes_per_step":
+                int(hdata.numel()) + 8 * (count + 1), "d2h_bytes_per_step": len(e2e_blob),
+                "same_bytes_as_device_build": e2e_same},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
-        "leaf_kernel_cfg": stats[-1]["leaf_cfg"],
-        "persistent_vs_per_bucket": per_bucket,
-        "rotation_fitting": rotation,
-        "query": query,
+        "query_s_all_keys": query_s,
+        "input_generation_s": gen_s,
         "wall_s_timed": wall,
+        "u64_1M_leaf48": u64rec,
     }
     if clocks:
         line["clocks"] = clocks
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline(24000, single_keys=4000)
+        import oracle
+        from oracle.sampled import sampled_parity
+
+        oracle.build()
+        data = hdata.numpy()
+        offs = hoffs.numpy().view(np.uint64)
+        lo, hi = oracle.fingerprints_str(data, offs)
+        cores = os.cpu_count() or 1
+        par = sampled_parity(blob, lo, hi, STR_LEAF, mode == pkg.SHK_LEAF_ROTATION, n_buckets=args.parity_buckets,
+                             n_leaves=args.parity_leaves, nthreads=cores)
+        line["oracle_parity_sampled"] = par
+        line["cpu_baseline"] = {"value": par["oracle_leaf_keys"] / par["oracle_leaf_s"], "unit": "keys/s",
+                                "cores": min(cores, par["sampled_leaves"]), "kind": "oracle",
+                                "sample": f"extrapolated per key from the oracle's leaf search of "
+                                          f"{par['sampled_leaves']} leaves drawn from {par['sampled_buckets']} "
+                                          f"random buckets of this build ({par['oracle_leaf_s']:.1f} s, OpenMP "
+                                          f"over leaves); the leaf search is the oracle's dominant cost at "
+                                          f"leaf size 64"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -503,105 +629,62 @@ def run_serve(args):
     return 0
 
 
-def run_strings(args):
-    """10^8 random strings (length uniform in [10, 50], bytes uniform in
-    [1, 127], stream seed 4) hashed to 128-bit fingerprints, leaf size 64,
-    bucket size 2000, rotation fitting with partial hash calculation.  One
-    timed build (after a warm-up build of the first 10^6 strings), then every
-    key is queried and the ranks checked to be a permutation of [0, N)."""
+def run_u64(args):
+    """The 10^6-key, leaf-48 build alone (its sub-record as one JSON line), for
+    profiling runs of the plain leaf kernel."""
     import torch
 
     import paper_2308_09561_gb300 as pkg
-    import shk_inputs
 
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
+    torch.cuda.set_device(_dist()[2])
     pkg.load_library()
-    count = args.keys or 100_000_000
-    t = time.perf_counter()
-    data, offs = shk_inputs.ascii_strings(count, 4 + 1000 * rank)
-    gen_s = time.perf_counter() - t
-    ddata = torch.from_numpy(data).cuda()
-    doffs = torch.from_numpy(offs.view(np.int64)).cuda()
-    leaf, mode = 64, (pkg.SHK_LEAF_ROTATION if args.leaf_mode == "rf" else pkg.SHK_LEAF_PLAIN)
-    w = min(count, 1_000_000)
-    eps = args.eps_num
-    pkg.shk_build(ddata, leaf, BUCKET, kind=pkg.SHK_KEYS_STR, str_offsets=doffs[:w + 1], leaf_mode=mode,
-                  eps_num=eps).close()
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        m = pkg.shk_build(ddata, leaf, BUCKET, kind=pkg.SHK_KEYS_STR, str_offsets=doffs, leaf_mode=mode,
-                          eps_num=eps, profile=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    st = m.stats()
-    blob = m.serialize()
-    tq = time.perf_counter()
-    ranks = m.query(ddata, kind=pkg.SHK_KEYS_STR, str_offsets=doffs)
-    torch.cuda.synchronize()
-    query_s = time.perf_counter() - tq
-    srt, _ = torch.sort(ranks)
-    bij = bool(torch.equal(srt, torch.arange(count, device="cuda", dtype=torch.int64)))
-    del srt, ranks
-    m.close()
-    # fingerprint + radix partition bytes: read the strings and their
-    # offsets, write one 16-byte fingerprint per key; the scatter reads it
-    # and writes it into its bucket
-    part_bytes = data.size + 8 * (count + 1) + 16 * count + 32 * count
-    part_ms = st["ms_fingerprint"] + st["ms_partition"]
-    line = {"metric": "MPHF build keys/s, 10^8 string keys, leaf 64", "value": count / (ms / 1e3),
-            "unit": "keys/s", "n_gpus": ws, "steps": 1, "warmup": 1, "ms_per_step": ms,
-            "higher_is_better": True, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "mphf_build_1e8_strings_leaf64_bucket2000", "keys": count,
-                       "string_bytes": int(data.size), "leaf_size": leaf, "bucket_size": BUCKET,
-                       "leaf_mode": args.leaf_mode, "eps_num": eps or "default"},
-            "bits_per_key": 8 * len(blob) / count, "bijection": bij, "query_s_all_keys": query_s,
-            "phase_ms": {k: st[k] for k in ("ms_fingerprint", "ms_partition", "ms_split", "ms_leaf",
-                                            "ms_orient", "ms_encode", "ms_ribbon", "ms_total")},
-            "partition_gbs": part_bytes / (part_ms / 1e3) / 1e9,
-            "leaf_candidates_per_s": st["leaf_seeds_min"] / (st["ms_leaf"] / 1e3),
-            "leaves": st["n_leaves"], "input_generation_s": gen_s}
-    clocks = clk.summary()
-    if clocks:
-        line["clocks"] = clocks
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 4 * 32 * float(_peaks().get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    cfg = {}
+    if args.leaf_cfg:
+        u, w, r = (int(v) for v in args.leaf_cfg.split(","))
+        cfg = {"seeds_per_lane": u, "warps_per_block": w, "key_unroll": r, "chunk_passes": 8}
+    global N_KEYS
+    N_KEYS = args.keys or N_KEYS
+    rec, _ = u64_subrecord(pkg, args, flush, torch.cuda.current_stream(), peak, cfg)
+    print(json.dumps(rec), flush=True)
     return 0
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-sample-keys", type=int, default=24000,
-                    help="reference arm: keys of the workload's stream the oracle builds per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle leg (sampled parity and cpu_baseline)")
+    ap.add_argument("--no-subrecords", action="store_true", help="skip the 10^6-key sub-record")
+    ap.add_argument("--ref-leaves", type=int, default=16,
+                    help="reference arm: leaves of the workload the oracle searches per step")
+    ap.add_argument("--parity-buckets", type=int, default=50, help="oracle leg: buckets compared")
+    ap.add_argument("--parity-leaves", type=int, default=64, help="oracle leg: leaves compared")
     ap.add_argument("--keys", type=int, default=None,
                     help="key (leafbatch: leaf) count other than the workload's own, for profiling runs")
     ap.add_argument("--compare-per-bucket", action="store_true",
-                    help="time the one-launch-per-bucket form on the whole workload (slow)")
+                    help="time the one-launch-per-bucket form on all 10^6 keys (slow)")
     ap.add_argument("--leaf-cfg", default="",
-                    help="build: fix the leaf kernel configuration 'U,W,R' (seeds per lane, warps per "
-                         "block, key unroll) instead of the autotuner's (for profiling runs)")
+                    help="plain builds: fix the leaf kernel configuration 'U,W,R' (seeds per lane, warps "
+                         "per block, key unroll) instead of the autotuner's (for profiling runs)")
     ap.add_argument("--requests", type=int, default=100, help="serve: number of requests")
     ap.add_argument("--max-keys", type=float, default=3e5,
                     help="serve: largest request (sizes log-uniform from 1e3; 1e7 in the full stream)")
     ap.add_argument("--serve-rf", action="store_true", help="serve: rotation-fitting leaves")
-    ap.add_argument("--eps-num", type=int, default=983,
-                    help="strings: retrieval overhead eps = eps_num / 65536 (default 983, ~1.5 %%, "
-                         "for ~1.54 bits/key; 0: the library default, 3277)")
+    ap.add_argument("--eps-num", type=int, default=STR_EPS,
+                    help="headline: retrieval overhead eps = eps_num / 65536 (default 983, ~1.5 %%)")
     ap.add_argument("--leafbatch-rf", dest="workload_leafbatch_rf", action="store_true",
                     help="leafbatch: rotation fitting (shk_leaf_search_rf)")
     ap.add_argument("--leaf-mode", default="rf", choices=["rf", "plain"],
-                    help="strings / leafbatch workloads: rotation fitting or plain leaves")
-    ap.add_argument("--workload", default="build", choices=["build", "leafbatch", "serve", "strings"],
-                    help="leafbatch: 65,536 independent leaves of 40..64 keys, one graph-replayed launch")
+                    help="headline / leafbatch workloads: rotation fitting or plain leaves")
+    ap.add_argument("--workload", default="build", choices=["build", "u64", "leafbatch", "serve"],
+                    help="build: the 10^8-string headline; u64: the 10^6-key leaf-48 build alone; "
+                         "leafbatch: 65,536 independent leaves of 40..64 keys; serve: served builds")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -609,8 +692,8 @@ def main():
         return run_leafbatch(args)
     if args.workload == "serve":
         return run_serve(args)
-    if args.workload == "strings":
-        return run_strings(args)
+    if args.workload == "u64":
+        return run_u64(args)
     return run_ours(args)
 
 

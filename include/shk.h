@@ -42,9 +42,9 @@ typedef enum {
   SHK_ENOMEM = 3,     /* a host or device allocation failed                     */
   SHK_ECUDA = 4,      /* a CUDA call failed; the message names it              */
   SHK_ESEEDCAP = 5,   /* a seed search reached its cap (never in practice)      */
-  SHK_ETIMEOUT = 6,   /* a bounded device wait gave up                          */
+  SHK_ETIMEOUT = 6,   /* a build's time budget (deadline_ms) ran out            */
   SHK_EFORMAT = 7,    /* a serialized MPHF is malformed                         */
-  SHK_ECANCELLED = 8  /* reserved for cancelled requests                        */
+  SHK_ECANCELLED = 8  /* a served request was cancelled (shk_server_cancel)     */
 } shk_status;
 
 typedef enum {
@@ -68,7 +68,9 @@ typedef struct {
 typedef enum {
   SHK_SCHED_PERSISTENT = 0,     /* one persistent launch over all leaves, work  */
                                 /* stealing over (leaf, seed-chunk) items       */
-  SHK_SCHED_PER_BUCKET = 1      /* one launch per bucket, one warp per leaf     */
+  SHK_SCHED_PER_BUCKET = 1,     /* one launch per bucket, one warp per leaf     */
+  SHK_SCHED_SINGLE_LAUNCH = 2   /* one launch over all leaves, one warp per     */
+                                /* leaf, no work sharing                        */
 } shk_sched;
 
 /* How leaves are solved (both are ShockHash: the smallest value whose graph
@@ -94,6 +96,11 @@ typedef struct {
   uint32_t warps_per_block;  /* with seeds_per_lane != 0: 4, 8 or 16; 0 = 8      */
   uint32_t key_unroll;       /* with seeds_per_lane != 0: 1, 2 or 4; 0 = 2       */
   uint32_t leaf_mode;        /* shk_leaf_mode; recorded in the encoded header     */
+  uint32_t deadline_ms;      /* 0 = none; else the leaf search stops once this    */
+                             /* many ms have passed since the build started on    */
+                             /* the device (checked once per work item, about    */
+                             /* every 0.1 ms) and the build fails with           */
+                             /* SHK_ETIMEOUT                                      */
 } shk_build_opts;
 
 /* Statistics of the build that produced an MPHF (shk_build_stats). */
@@ -128,6 +135,16 @@ typedef struct {
                                 /* 8 ceil(T/8) x E[min(cells A misses, 24 (m =   */
                                 /* 64) or 20)] given |A| (exact expectation for  */
                                 /* ideal hashing); 0 otherwise                  */
+  uint64_t leaf_seeds_tested;   /* seeds a sequential search tests: sum of seed  */
+                                /* + 1 (plain) or floor(v/m) + 1 (rotation       */
+                                /* fitting) over leaves                         */
+  uint64_t leaf_t0_ns, leaf_t1_ns; /* device global timer (ns) when the first    */
+                                /* leaf-search block started and the last one   */
+                                /* ended (persistent schedule): lets concurrent */
+                                /* builds' kernels be compared on one clock     */
+  uint64_t device_bytes_peak;   /* high watermark of the library's device memory */
+                                /* pool during the build, plus the result; only  */
+                                /* a build that runs alone reads its own peak    */
 } shk_stats;
 
 typedef struct shk_mphf shk_mphf;
@@ -269,8 +286,10 @@ typedef struct {
  * (0 = 4). */
 shk_status shk_server_create(uint64_t hbm_budget_bytes, uint32_t workers, shk_server** out);
 
-/* shk_server_submit -- queue a build.  keys are copied before the call returns
- * (host or device buffers); opts as for shk_build.  *req_id identifies it. */
+/* shk_server_submit -- queue a build.  keys are copied before the call returns:
+ * host keys into host memory, device keys into the library's device memory
+ * pool on the server's device (they never pass through the host); opts as for
+ * shk_build.  *req_id identifies it. */
 shk_status shk_server_submit(shk_server* srv, const shk_keys* keys, const shk_build_opts* opts,
                              uint64_t* req_id);
 
@@ -286,6 +305,20 @@ shk_status shk_server_poll(shk_server* srv, uint64_t req_id, shk_mphf** out,
  * request id). */
 shk_status shk_server_wait(shk_server* srv, uint64_t req_id, shk_mphf** out,
                            shk_request_info* info);
+
+/* shk_server_cancel -- cancel a request.  A queued request never runs; a
+ * running one stops its leaf search at its next work item (the build's
+ * kernels poll a host-mapped flag).  Either way the request completes with
+ * status SHK_ECANCELLED and no MPHF (also if its build had already finished
+ * but was not yet collected).  A finished request is left as it is.
+ * SHK_EINVAL for an unknown request id. */
+shk_status shk_server_cancel(shk_server* srv, uint64_t req_id);
+
+/* shk_build_footprint -- the device bytes the server reserves for a build of
+ * these keys with these options (the admission estimate): the keys as
+ * staged, 80 bytes per key, 96 per bucket and 8 MiB.  A build that runs
+ * alone reports its measured peak in shk_stats.device_bytes_peak. */
+shk_status shk_build_footprint(const shk_keys* keys, const shk_build_opts* opts, uint64_t* bytes);
 
 /* shk_server_get_stats -- counters and the device-memory reservation. */
 shk_status shk_server_get_stats(shk_server* srv, shk_server_stats* out);

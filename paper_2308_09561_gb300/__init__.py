@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libshk_gpu.so")
 
 SHK_OK, SHK_EINVAL, SHK_EDUPKEY, SHK_ENOMEM, SHK_ECUDA, SHK_ESEEDCAP, SHK_ETIMEOUT, SHK_EFORMAT = range(8)
 SHK_KEYS_U64, SHK_KEYS_STR, SHK_KEYS_FP128 = 0, 1, 2
-SHK_SCHED_PERSISTENT, SHK_SCHED_PER_BUCKET = 0, 1
+SHK_SCHED_PERSISTENT, SHK_SCHED_PER_BUCKET, SHK_SCHED_SINGLE_LAUNCH = 0, 1, 2
 SHK_LEAF_PLAIN, SHK_LEAF_ROTATION = 0, 1
 
 # exported symbols declared in include/shk.h
@@ -30,7 +30,8 @@ EXPORTS = ("shk_build", "shk_build_stats", "shk_query", "shk_serialize", "shk_de
            "shk_leaf_tune", "shk_leaf_configs", "shk_leaf_graph_replays", "shk_leaf_search_rf",
            "shk_server_create",
            "shk_server_submit", "shk_server_poll", "shk_server_wait", "shk_server_get_stats",
-           "shk_server_destroy", "shk_version", "shk_release_memory", "shk_int_issue_rate")
+           "shk_server_destroy", "shk_version", "shk_release_memory", "shk_int_issue_rate",
+           "shk_server_cancel", "shk_build_footprint")
 
 
 class ShkError(RuntimeError):
@@ -47,7 +48,7 @@ class _Keys(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in
                 ("leaf_size", "bucket_size", "shard_buckets", "eps_num", "sched", "seeds_per_lane",
-                 "chunk_passes", "profile", "warps_per_block", "key_unroll", "leaf_mode")]
+                 "chunk_passes", "profile", "warps_per_block", "key_unroll", "leaf_mode", "deadline_ms")]
 
 
 _STAT_U64 = ["n_keys", "n_buckets", "n_leaves", "n_search_leaves", "n_split_nodes", "leaf_seeds_min",
@@ -59,7 +60,9 @@ _STAT_F64 = ["ms_fingerprint", "ms_partition", "ms_split", "ms_leaf", "ms_orient
 class _Stats(ctypes.Structure):
     _fields_ = ([(n, ctypes.c_uint64) for n in _STAT_U64] + [(n, ctypes.c_double) for n in _STAT_F64]
                 + [("leaf_launches", ctypes.c_uint64), ("leaf_cfg", ctypes.c_uint32 * 4),
-                   ("leaf_hash_evals", ctypes.c_uint64), ("leaf_rf_cells", ctypes.c_double)])
+                   ("leaf_hash_evals", ctypes.c_uint64), ("leaf_rf_cells", ctypes.c_double),
+                   ("leaf_seeds_tested", ctypes.c_uint64), ("leaf_t0_ns", ctypes.c_uint64),
+                   ("leaf_t1_ns", ctypes.c_uint64), ("device_bytes_peak", ctypes.c_uint64)])
 
 
 class _ReqInfo(ctypes.Structure):
@@ -106,6 +109,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "shk_server_wait": (i32, [vp, u64, ctypes.POINTER(vp), ctypes.POINTER(_ReqInfo)]),
         "shk_server_get_stats": (i32, [vp, ctypes.POINTER(_SrvStats)]),
         "shk_server_destroy": (None, [vp]),
+        "shk_server_cancel": (i32, [vp, u64]),
+        "shk_build_footprint": (i32, [ctypes.POINTER(_Keys), ctypes.POINTER(_Opts), ctypes.POINTER(u64)]),
         "shk_version": (ctypes.c_char_p, []),
         "shk_release_memory": (None, []),
         "shk_int_issue_rate": (i32, [u32, u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -217,15 +222,22 @@ class Mphf:
         return shk_query(self.handle, keys, kind=kind, str_offsets=str_offsets, out=out, stream=stream)
 
 
+def _opts(leaf_size, bucket_size, shard_buckets=0, eps_num=0, sched=SHK_SCHED_PERSISTENT, seeds_per_lane=0,
+          chunk_passes=0, profile=False, warps_per_block=0, key_unroll=0, leaf_mode=SHK_LEAF_PLAIN,
+          deadline_ms=0) -> _Opts:
+    return _Opts(leaf_size, bucket_size, shard_buckets, eps_num, sched, seeds_per_lane, chunk_passes,
+                 1 if profile else 0, warps_per_block, key_unroll, leaf_mode, deadline_ms)
+
+
 def shk_build(keys, leaf_size: int, bucket_size: int, *, kind: int = SHK_KEYS_U64, str_offsets=None,
               shard_buckets: int = 0, eps_num: int = 0, sched: int = SHK_SCHED_PERSISTENT,
               seeds_per_lane: int = 0, chunk_passes: int = 0, profile: bool = False,
               warps_per_block: int = 0, key_unroll: int = 0, leaf_mode: int = SHK_LEAF_PLAIN,
-              stream=None) -> Mphf:
+              deadline_ms: int = 0, stream=None) -> Mphf:
     lib = load_library()
     k, keep = _as_keys(keys, kind, str_offsets)
-    o = _Opts(leaf_size, bucket_size, shard_buckets, eps_num, sched, seeds_per_lane, chunk_passes,
-              1 if profile else 0, warps_per_block, key_unroll, leaf_mode)
+    o = _opts(leaf_size, bucket_size, shard_buckets, eps_num, sched, seeds_per_lane, chunk_passes, profile,
+              warps_per_block, key_unroll, leaf_mode, deadline_ms)
     out = ctypes.c_void_p()
     _check(lib.shk_build(ctypes.byref(k), ctypes.byref(o), _stream_handle(stream), ctypes.byref(out)))
     del keep
@@ -412,9 +424,7 @@ def shk_server_create(hbm_budget_bytes: int = 0, workers: int = 0) -> int:
 def shk_server_submit(server: int, keys, leaf_size: int, bucket_size: int, *, kind: int = SHK_KEYS_U64,
                       str_offsets=None, **opt) -> int:
     k, keep = _as_keys(keys, kind, str_offsets)
-    o = _Opts(leaf_size, bucket_size, opt.get("shard_buckets", 0), opt.get("eps_num", 0), opt.get("sched", 0),
-              opt.get("seeds_per_lane", 0), opt.get("chunk_passes", 0), 0, opt.get("warps_per_block", 0),
-              opt.get("key_unroll", 0), opt.get("leaf_mode", 0))
+    o = _opts(leaf_size, bucket_size, **opt)
     rid = ctypes.c_uint64()
     _check(load_library().shk_server_submit(server, ctypes.byref(k), ctypes.byref(o), ctypes.byref(rid)))
     del keep
@@ -444,6 +454,21 @@ def shk_server_get_stats(server: int) -> dict:
     s = _SrvStats()
     _check(load_library().shk_server_get_stats(server, ctypes.byref(s)))
     return {name: getattr(s, name) for name, _ in _SrvStats._fields_}
+
+
+def shk_server_cancel(server: int, req_id: int) -> None:
+    _check(load_library().shk_server_cancel(server, req_id))
+
+
+def shk_build_footprint(keys, leaf_size: int, bucket_size: int, *, kind: int = SHK_KEYS_U64, str_offsets=None,
+                        **opt) -> int:
+    """The server's device-memory estimate for a build of these keys."""
+    k, keep = _as_keys(keys, kind, str_offsets)
+    o = _opts(leaf_size, bucket_size, **opt)
+    out = ctypes.c_uint64()
+    _check(load_library().shk_build_footprint(ctypes.byref(k), ctypes.byref(o), ctypes.byref(out)))
+    del keep
+    return out.value
 
 
 def shk_server_destroy(server: int) -> None:

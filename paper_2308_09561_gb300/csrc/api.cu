@@ -33,7 +33,7 @@ shk_status fail(shk_status st, const std::string& msg) {
 static std::mutex g_pool_mu;
 static cudaMemPool_t g_pool[64];
 
-cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s) {
+static cudaError_t pool_of_current(cudaMemPool_t* out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -59,7 +59,33 @@ cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s) {
     }
     pool = g_pool[dev];
   }
+  *out = pool;
+  return cudaSuccess;
+}
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool;
+  const cudaError_t e = pool_of_current(&pool);
+  if (e != cudaSuccess) return e;
   return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+// High watermark of the current device's pool (reset: the watermark restarts
+// from the bytes in use now).
+static uint64_t pool_used_high(bool reset) {
+  cudaMemPool_t pool;
+  if (pool_of_current(&pool) != cudaSuccess) return 0;
+  uint64_t v = 0;
+  if (reset) {
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v);
+    return 0;
+  }
+  cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v);
+  return v;
+}
+
+__global__ void k_set_deadline(unsigned long long* at, uint64_t budget_ns) {
+  *at = global_ns() + budget_ns;
 }
 
 shk_status init_ctx(Ctx& c) {
@@ -69,6 +95,8 @@ shk_status init_ctx(Ctx& c) {
 }
 
 static shk_status device_errors(uint32_t e) {
+  if (e & kErrCancelled) return fail(SHK_ECANCELLED, "the build was cancelled");
+  if (e & kErrTimeout) return fail(SHK_ETIMEOUT, "the build's time budget (deadline_ms) ran out");
   if (e & kErrDup) return fail(SHK_EDUPKEY, "two keys have the same 128-bit fingerprint");
   if (e & kErrBucketOverflow) return fail(SHK_EINVAL, "a bucket holds more than 8192 keys");
   if (e & kErrLeafSize) return fail(SHK_EINVAL, "a leaf has 0 or more than 64 keys");
@@ -225,15 +253,15 @@ static shk_status check_keys(const shk_keys* keys) {
   return SHK_OK;
 }
 
-static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cudaStream_t st,
-                             shk_mphf** out) {
+shk_status build_controlled(const shk_keys* keys, const shk_build_opts* o, cudaStream_t st,
+                            shk_mphf** out, const volatile uint32_t* abort) {
   SHK_TRY(check_keys(keys));
   const uint64_t N = keys->n_keys;
   const uint32_t n = o->leaf_size, b = o->bucket_size;
   if (n < 2 || n > kMaxLeaf) return fail(SHK_EINVAL, "leaf_size must be in [2, 64]");
   if (b < n || b > kMaxBucketSize) return fail(SHK_EINVAL, "bucket_size must be in [leaf_size, 4096]");
   if (N >= (1ull << 32)) return fail(SHK_EINVAL, "at most 2^32 - 1 keys");
-  if (o->sched > SHK_SCHED_PER_BUCKET) return fail(SHK_EINVAL, "unknown schedule");
+  if (o->sched > SHK_SCHED_SINGLE_LAUNCH) return fail(SHK_EINVAL, "unknown schedule");
   if (o->leaf_mode > SHK_LEAF_ROTATION) return fail(SHK_EINVAL, "unknown leaf mode");
   const uint32_t rf = o->leaf_mode;
   const uint32_t S = o->shard_buckets ? o->shard_buckets : std::max(1u, 8192u / b);
@@ -254,6 +282,18 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
     if (o->chunk_passes) cfg.passes = o->chunk_passes;
   }
   PhaseTimer pt(o->profile != 0, st);
+  pool_used_high(true);
+  // leaf-search control: [0], [1] device start / end of the leaf search,
+  // [2] deadline (device time)
+  unsigned long long* ctl;
+  SHK_TRY(c.arena.alloc(&ctl, 4));
+  SHK_CUDA(cudaMemsetAsync(ctl, 0xFF, 8, st));
+  SHK_CUDA(cudaMemsetAsync(ctl + 1, 0, 24, st));
+  if (o->deadline_ms) {
+    k_set_deadline<<<1, 1, 0, st>>>(ctl + 2, (uint64_t)o->deadline_ms * 1000000ull);
+    c.launches++;
+    SHK_CUDA(cudaGetLastError());
+  }
   const int t0 = pt.mark();
   const uint64_t B = N ? (N + b - 1) / b : 0;
   const uint32_t N32 = (uint32_t)N;
@@ -326,13 +366,18 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   // a4 + a5: leaf seeds
   unsigned long long *best, *counters;
   SHK_TRY(c.arena.alloc(&best, h_L));
-  // executed, sum(seed+1), sum((seed+1) m), hash evaluations, rotation-filter steps (double)
-  SHK_TRY(c.arena.alloc(&counters, 5, true));
+  // executed, sum(seed+1), sum((seed+1) m), hash evaluations, seeds tested,
+  // rotation-filter steps (double)
+  SHK_TRY(c.arena.alloc(&counters, 6, true));
   if (h_L) SHK_CUDA(cudaMemsetAsync(best, 0xFF, (size_t)h_L * 8, st));
-  LeafSearchArgs a{leaves, h_L, llo, 0, best, err, counters, cfg};
+  LeafSearchArgs a{leaves, h_L, llo, 0, best, err, counters, cfg,
+                   LeafCtl{ctl, o->deadline_ms ? ctl + 2 : nullptr, abort}};
   uint64_t leaf_launches = 0;
   if (o->sched == SHK_SCHED_PERSISTENT) {
     SHK_TRY(rf ? launch_leaf_rf_persistent(c, a) : launch_leaf_persistent(c, a));
+    leaf_launches = h_L ? 1 : 0;
+  } else if (o->sched == SHK_SCHED_SINGLE_LAUNCH) {
+    SHK_TRY(rf ? launch_leaf_rf_range(c, a, 0, h_L) : launch_leaf_range(c, a, 0, h_L));
     leaf_launches = h_L ? 1 : 0;
   } else {
     for (uint64_t i = 0; i < B; i++) {
@@ -349,7 +394,7 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   uint8_t* f;
   SHK_TRY(c.arena.alloc(&f, N, true));
   SHK_TRY(launch_orient(c, leaves, h_L, llo, best, codes, f, nullptr, err, rf));
-  SHK_TRY(launch_leaf_sums(c, leaves, h_L, best, counters + 1, rf, llo, (double*)(counters + 4)));
+  SHK_TRY(launch_leaf_sums(c, leaves, h_L, best, counters + 1, rf, llo, (double*)(counters + 5)));
   const int t5 = pt.mark();
 
   // a7 sizes: Rice bits per bucket, shard slots
@@ -368,11 +413,12 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   SHK_TRY(launch_max_shard_keys(c, K, B, S, num_shards, max_sk));
   uint64_t h_rice_bits = 0, h_rib_bits = 0;
   uint32_t h_max_sk = 0;
-  unsigned long long h_cnt[5] = {0, 0, 0, 0, 0};
+  unsigned long long h_cnt[6] = {0, 0, 0, 0, 0, 0}, h_ctl[2] = {0, 0};
   SHK_TRY(d2h(c, &h_rice_bits, O + B));
   SHK_TRY(d2h(c, &h_rib_bits, shard_off + num_shards));
   SHK_TRY(d2h(c, &h_max_sk, max_sk));
-  SHK_TRY(d2h(c, h_cnt, counters, 5));
+  SHK_TRY(d2h(c, h_cnt, counters, 6));
+  SHK_TRY(d2h(c, h_ctl, ctl, 2));
   SHK_TRY(d2h(c, &h_err, err));
   SHK_CUDA(cudaStreamSynchronize(st));
   SHK_TRY(device_errors(h_err));
@@ -439,7 +485,11 @@ static shk_status build_impl(const shk_keys* keys, const shk_build_opts* o, cuda
   s.leaf_seeds_min = h_cnt[1];
   s.leaf_key_evals = h_cnt[2];
   s.leaf_hash_evals = h_cnt[3];
-  memcpy(&s.leaf_rf_cells, &h_cnt[4], sizeof(double));
+  s.leaf_seeds_tested = h_cnt[4];
+  memcpy(&s.leaf_rf_cells, &h_cnt[5], sizeof(double));
+  s.leaf_t0_ns = h_L ? h_ctl[0] : 0;
+  s.leaf_t1_ns = h_ctl[1];
+  s.device_bytes_peak = pool_used_high(false) + m->words * 8 + (B + 1) * 12 + (num_shards + 1) * 8;
   s.kernel_launches = c.launches;
   s.leaf_launches = leaf_launches;
   s.size_bits = m->words * 64;
@@ -478,7 +528,8 @@ extern "C" shk_status shk_build(const shk_keys* keys, const shk_build_opts* opts
   if (!out || !opts) return fail(SHK_EINVAL, "NULL argument");
   *out = nullptr;
   g_last_error.clear();
-  shk_status st = no_throw([&] { return build_impl(keys, opts, (cudaStream_t)cuda_stream, out); });
+  shk_status st =
+      no_throw([&] { return build_controlled(keys, opts, (cudaStream_t)cuda_stream, out, nullptr); });
   if (st != SHK_OK) cudaStreamSynchronize((cudaStream_t)cuda_stream);
   return st;
 }

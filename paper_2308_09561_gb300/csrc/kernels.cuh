@@ -18,6 +18,12 @@ struct Ctx {
 
 shk_status init_ctx(Ctx& c);
 
+// shk_build with an abort flag (host-mapped memory, may be NULL) that stops
+// the leaf search with SHK_ECANCELLED once it is non-zero (the server's
+// cancellation).
+shk_status build_controlled(const shk_keys* keys, const shk_build_opts* o, cudaStream_t st,
+                            shk_mphf** out, const volatile uint32_t* abort);
+
 template <class Tin, class T>
 shk_status exclusive_scan(Ctx& c, const Tin* in, uint64_t n, T* out);
 
@@ -48,6 +54,17 @@ shk_status launch_split(Ctx& c, const ulonglong2* sfp, const uint32_t* K, uint64
 struct LeafCfg {
   uint32_t seeds_per_lane, warps, unroll, passes;
 };
+// Control of a leaf search (every pointer may be NULL): t_range[0] / [1]
+// receive the device time the first block started / the last warp ended
+// (atomicMin / atomicMax; preset to ~0 / 0); the search stops, setting
+// kErrTimeout, once the device time passes *deadline (0 = none), or, setting
+// kErrCancelled, once *abort is non-zero (host-mapped memory).  Both are
+// checked before every work item.
+struct LeafCtl {
+  unsigned long long* t_range;
+  const unsigned long long* deadline;
+  const volatile uint32_t* abort;
+};
 struct LeafSearchArgs {
   const LeafDesc* leaves;
   uint32_t n_leaves;
@@ -57,7 +74,31 @@ struct LeafSearchArgs {
   uint32_t* err;
   unsigned long long* executed;  // seeds evaluated (counter)
   LeafCfg cfg;
+  LeafCtl ctl;
 };
+
+// Warp-uniform: true when the search must stop (sets the error flag).
+__device__ __forceinline__ bool leaf_should_stop(const LeafCtl& ctl, uint32_t* err) {
+  int stop = 0;
+  if ((threadIdx.x & 31) == 0) {
+    if (ctl.abort && *ctl.abort) {
+      atomicOr(err, kErrCancelled);
+      stop = 1;
+    } else if (ctl.deadline && *ctl.deadline && global_ns() > *ctl.deadline) {
+      atomicOr(err, kErrTimeout);
+      stop = 1;
+    }
+  }
+  return __shfl_sync(0xFFFFFFFFu, stop, 0) != 0;
+}
+
+__device__ __forceinline__ void leaf_mark_start(const LeafCtl& ctl) {
+  if (ctl.t_range && threadIdx.x == 0) atomicMin(&ctl.t_range[0], (unsigned long long)global_ns());
+}
+
+__device__ __forceinline__ void leaf_mark_end(const LeafCtl& ctl) {
+  if (ctl.t_range && (threadIdx.x & 31) == 0) atomicMax(&ctl.t_range[1], (unsigned long long)global_ns());
+}
 shk_status launch_leaf_persistent(Ctx& c, const LeafSearchArgs& a);
 // As launch_leaf_persistent, with caller-owned state of
 // (n_leaves + (n_leaves + 31) / 32 + 1) u32 words (cleared by the launch).
@@ -77,8 +118,9 @@ shk_status launch_orient(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves, cons
 // rotation fitting (leaf mode 1): best[] receives v = s*m + r
 shk_status launch_leaf_rf_persistent(Ctx& c, const LeafSearchArgs& a);
 shk_status launch_leaf_rf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint32_t l1);
-// sums[0..2] += sum (value + 1), sum (value + 1) m, hash evaluations of a
-// sequential search; *cells += rotation-filter steps (leaf mode 1)
+// sums[0..3] += sum (value + 1), sum (value + 1) m, hash evaluations and
+// seeds tested by a sequential search; *cells += rotation-filter steps
+// (leaf mode 1)
 shk_status launch_leaf_sums(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves,
                             const unsigned long long* best, unsigned long long* sums,
                             uint32_t leaf_mode, const uint64_t* x, double* cells);

@@ -215,16 +215,18 @@ __global__ void __launch_bounds__(WARPS * 32)
     k_leaf_persistent(const LeafDesc* __restrict__ leaves, uint32_t n_leaves,
                       const uint64_t* __restrict__ x, uint64_t seed_start, uint32_t passes,
                       unsigned long long* best, uint32_t* next_chunk, uint32_t* closed,
-                      uint32_t* next_leaf, unsigned long long* executed, uint32_t* err) {
+                      uint32_t* next_leaf, unsigned long long* executed, uint32_t* err, LeafCtl ctl) {
   __shared__ WarpScratch scratch[WARPS];
   const uint32_t lane = threadIdx.x & 31;
   WarpScratch* ws = &scratch[threadIdx.x >> 5];
   const uint32_t gw = blockIdx.x * WARPS + (threadIdx.x >> 5);
+  leaf_mark_start(ctl);
+  bool stop = false;
   const uint32_t nwords = (n_leaves + 31) / 32;
   uint32_t pos = nwords ? (uint32_t)(((uint64_t)gw * 2654435761u) % nwords) : 0;
   const uint64_t chunk = (uint64_t)passes * 32u * U;
   unsigned long long done_seeds = 0;
-  for (;;) {
+  while (!stop) {
     uint32_t leaf = 0;
     if (lane == 0) leaf = atomicAdd(next_leaf, 1u);
     leaf = __shfl_sync(kFull, leaf, 0);
@@ -245,6 +247,10 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
     load_leaf(ws, d, x);
     for (;;) {
+      if (leaf_should_stop(ctl, err)) {
+        stop = true;
+        break;
+      }
       uint32_t ci = 0;
       if (lane == 0) ci = atomicAdd(&next_chunk[leaf], 1u);
       ci = __shfl_sync(kFull, ci, 0);
@@ -271,6 +277,7 @@ __global__ void __launch_bounds__(WARPS * 32)
     __syncwarp();
   }
   if (lane == 0 && done_seeds) atomicAdd(executed, done_seeds);
+  leaf_mark_end(ctl);
 }
 
 // One warp per leaf, no sharing: the plain form that is launched once per
@@ -279,7 +286,8 @@ template <int U, int WARPS, int UNROLL>
 __global__ void __launch_bounds__(WARPS * 32)
     k_leaf_range(const LeafDesc* __restrict__ leaves, uint32_t l0, uint32_t l1,
                  const uint64_t* __restrict__ x, uint64_t seed_start, uint32_t passes,
-                 unsigned long long* best, unsigned long long* executed, uint32_t* err) {
+                 unsigned long long* best, unsigned long long* executed, uint32_t* err,
+                 LeafCtl ctl) {
   __shared__ WarpScratch scratch[WARPS];
   const uint32_t lane = threadIdx.x & 31;
   WarpScratch* ws = &scratch[threadIdx.x >> 5];
@@ -294,6 +302,7 @@ __global__ void __launch_bounds__(WARPS * 32)
       if (lane == 0) atomicOr(err, kErrSeedCap);
       break;
     }
+    if (leaf_should_stop(ctl, err)) break;
     uint32_t done = 0;
     const uint64_t r = search_dispatch<U, UNROLL>(ws, d.m, s0, passes, nullptr, &done);
     done_seeds += done;
@@ -318,9 +327,9 @@ struct LeafKernels {
   LeafCfg cfg;
   void (*persistent)(const LeafDesc*, uint32_t, const uint64_t*, uint64_t, uint32_t,
                      unsigned long long*, uint32_t*, uint32_t*, uint32_t*, unsigned long long*,
-                     uint32_t*);
+                     uint32_t*, LeafCtl);
   void (*range)(const LeafDesc*, uint32_t, uint32_t, const uint64_t*, uint64_t, uint32_t,
-                unsigned long long*, unsigned long long*, uint32_t*);
+                unsigned long long*, unsigned long long*, uint32_t*, LeafCtl);
 };
 
 #define SHK_LEAF_CFG(U, W, R) {{U, W, R, 0}, k_leaf_persistent<U, W, R>, k_leaf_range<U, W, R>}
@@ -368,7 +377,7 @@ static shk_status launch_persistent_with(Ctx& c, const LeafSearchArgs& a, uint32
   SHK_TRY(persistent_blocks(c, k, &blocks));
   k->persistent<<<blocks, k->cfg.warps * 32, 0, c.stream>>>(
       a.leaves, L, a.x, a.seed_start, a.cfg.passes, a.best, state, state + L, state + L + nwords,
-      a.executed, a.err);
+      a.executed, a.err, a.ctl);
   c.launches++;
   SHK_CUDA(cudaGetLastError());
   return SHK_OK;
@@ -401,7 +410,7 @@ shk_status launch_leaf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, uint3
   const uint32_t W = k->cfg.warps;
   const uint32_t blocks = (l1 - l0 + W - 1) / W;
   k->range<<<blocks, W * 32, 0, c.stream>>>(a.leaves, l0, l1, a.x, a.seed_start, a.cfg.passes,
-                                            a.best, a.executed, a.err);
+                                            a.best, a.executed, a.err, a.ctl);
   c.launches++;
   SHK_CUDA(cudaGetLastError());
   return SHK_OK;
@@ -468,7 +477,7 @@ shk_status probe_leaf_cfg(Ctx& c, const LeafCfg& cfg, uint32_t m, double* evals_
     SHK_CUDA(cudaEventRecord(e0, c.stream));
     k->persistent<<<blocks, cfg.warps * 32, 0, c.stream>>>(descs, L, keys, kSeedCap - 4096, passes,
                                                           best, state, state + L, state + L + nwords,
-                                                          cnt, err);
+                                                          cnt, err, LeafCtl{});
     SHK_CUDA(cudaEventRecord(e1, c.stream));
     c.launches++;
     unsigned long long h = 0;
@@ -615,14 +624,15 @@ shk_status launch_orient(Ctx& c, const LeafDesc* leaves, uint32_t n_leaves, cons
 
 // Sums over leaves, counted from the results: sums[0] = sum (value + 1),
 // sums[1] = sum (value + 1) * m, sums[2] = the hash evaluations of a
-// sequential search, and (rotation fitting) *cells = its (seed, missed cell)
+// sequential search, sums[3] = its seeds tested (plain: value + 1; rotation
+// fitting: floor(value / m) + 1), and (rotation fitting) *cells = its (seed, missed cell)
 // steps of the rotation filter; cbar[m * 65 + a] = E[min(cells missed by a
 // set A of a keys, K)] for m > 32 (see rf_cell_table).
 __global__ void k_leaf_sums(const LeafDesc* leaves, uint32_t n_leaves,
                             const unsigned long long* best, unsigned long long* sums,
                             uint32_t leaf_mode, const uint64_t* x, const double* cbar,
                             double* cells) {
-  unsigned long long a = 0, b = 0, h = 0;
+  unsigned long long a = 0, b = 0, h = 0, tested = 0;
   double cl = 0;
   for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n_leaves;
        l += gridDim.x * blockDim.x) {
@@ -632,8 +642,10 @@ __global__ void k_leaf_sums(const LeafDesc* leaves, uint32_t n_leaves,
     b += s * d.m;
     if (leaf_mode == 0 || d.m < 2) {
       h += s * d.m;
+      tested += s;
     } else {
       const unsigned long long T = best[l] / d.m + 1;
+      tested += T;
       if (d.m > 32) {
         uint32_t na = 0;
         for (uint32_t i = 0; i < d.m; i++) na += (mix64(x[d.key_off + i] ^ kRfSalt) >> 63) == 0;
@@ -649,12 +661,14 @@ __global__ void k_leaf_sums(const LeafDesc* leaves, uint32_t n_leaves,
     a += __shfl_down_sync(kFull, a, o);
     b += __shfl_down_sync(kFull, b, o);
     h += __shfl_down_sync(kFull, h, o);
+    tested += __shfl_down_sync(kFull, tested, o);
     cl += __shfl_down_sync(kFull, cl, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(&sums[0], a);
     atomicAdd(&sums[1], b);
     atomicAdd(&sums[2], h);
+    atomicAdd(&sums[3], tested);
     if (cells) atomicAdd(cells, cl);
   }
 }

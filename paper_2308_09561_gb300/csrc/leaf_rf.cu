@@ -423,16 +423,19 @@ __global__ void __launch_bounds__(kRfWarps * 32, SHK_RF_MIN_BLOCKS)
     k_leaf_rf_persistent(const LeafDesc* __restrict__ leaves, uint32_t n_leaves,
                          const uint64_t* __restrict__ x, uint32_t passes,
                          unsigned long long* best, uint32_t* next_chunk, uint32_t* closed,
-                         uint32_t* next_leaf, unsigned long long* executed, uint32_t* err) {
+                         uint32_t* next_leaf, unsigned long long* executed, uint32_t* err,
+                         LeafCtl ctl) {
   __shared__ RfScratch scratch[kRfWarps];
   const uint32_t lane = threadIdx.x & 31;
   RfScratch* ws = &scratch[threadIdx.x >> 5];
   const uint32_t gw = blockIdx.x * kRfWarps + (threadIdx.x >> 5);
+  leaf_mark_start(ctl);
+  bool stop = false;
   const uint32_t nwords = (n_leaves + 31) / 32;
   uint32_t pos = nwords ? (uint32_t)(((uint64_t)gw * 2654435761u) % nwords) : 0;
   const uint64_t chunk = (uint64_t)passes * 32u * kRfSeeds;
   unsigned long long done_seeds = 0;
-  for (;;) {
+  while (!stop) {
     uint32_t leaf = 0;
     if (lane == 0) leaf = atomicAdd(next_leaf, 1u);
     leaf = __shfl_sync(kFullMask, leaf, 0);
@@ -454,6 +457,10 @@ __global__ void __launch_bounds__(kRfWarps * 32, SHK_RF_MIN_BLOCKS)
     const uint32_t na = load_leaf_rf(ws, d, x);
     const uint64_t cap = kSeedCap / d.m;
     for (;;) {
+      if (leaf_should_stop(ctl, err)) {
+        stop = true;
+        break;
+      }
       uint32_t ci = 0;
       if (lane == 0) ci = atomicAdd(&next_chunk[leaf], 1u);
       ci = __shfl_sync(kFullMask, ci, 0);
@@ -480,13 +487,14 @@ __global__ void __launch_bounds__(kRfWarps * 32, SHK_RF_MIN_BLOCKS)
     __syncwarp();
   }
   if (lane == 0 && done_seeds) atomicAdd(executed, done_seeds);
+  leaf_mark_end(ctl);
 }
 
 // The plain form: one warp per leaf, one launch per bucket.
 __global__ void __launch_bounds__(kRfWarps * 32)
     k_leaf_rf_range(const LeafDesc* __restrict__ leaves, uint32_t l0, uint32_t l1,
                     const uint64_t* __restrict__ x, uint32_t passes, unsigned long long* best,
-                    unsigned long long* executed, uint32_t* err) {
+                    unsigned long long* executed, uint32_t* err, LeafCtl ctl) {
   __shared__ RfScratch scratch[kRfWarps];
   const uint32_t lane = threadIdx.x & 31;
   RfScratch* ws = &scratch[threadIdx.x >> 5];
@@ -502,6 +510,7 @@ __global__ void __launch_bounds__(kRfWarps * 32)
       if (lane == 0) atomicOr(err, kErrSeedCap);
       break;
     }
+    if (leaf_should_stop(ctl, err)) break;
     uint32_t done = 0;
     const uint64_t r = search_rf_dispatch(ws, d.m, na, s0, passes, nullptr, &done);
     done_seeds += done;
@@ -529,7 +538,7 @@ shk_status launch_leaf_rf_persistent(Ctx& c, const LeafSearchArgs& a) {
   const uint32_t blocks = (uint32_t)(c.num_sms * per_sm);
   k_leaf_rf_persistent<<<blocks, kRfWarps * 32, 0, c.stream>>>(
       a.leaves, L, a.x, a.cfg.passes, a.best, state, state + L, state + L + nwords, a.executed,
-      a.err);
+      a.err, a.ctl);
   c.launches++;
   SHK_CUDA(cudaGetLastError());
   return SHK_OK;
@@ -541,7 +550,7 @@ shk_status launch_leaf_rf_range(Ctx& c, const LeafSearchArgs& a, uint32_t l0, ui
     return fail(SHK_EINVAL, "seed, counter and key buffers must be 8-byte aligned");
   const uint32_t blocks = (l1 - l0 + kRfWarps - 1) / kRfWarps;
   k_leaf_rf_range<<<blocks, kRfWarps * 32, 0, c.stream>>>(a.leaves, l0, l1, a.x, a.cfg.passes,
-                                                           a.best, a.executed, a.err);
+                                                           a.best, a.executed, a.err, a.ctl);
   c.launches++;
   SHK_CUDA(cudaGetLastError());
   return SHK_OK;

@@ -30,13 +30,23 @@ uint64_t now_ns() {
 struct Request {
   uint64_t id = 0;
   int32_t kind = 0;
-  std::vector<uint8_t> data;      // host copy of the keys
+  std::vector<uint8_t> data;      // host copy of host keys
   std::vector<uint64_t> offsets;  // string keys
+  void* d_data = nullptr;         // device copy of device keys (library pool)
+  uint64_t* d_offsets = nullptr;
   uint64_t n_keys = 0;
   shk_build_opts opts{};
   shk_request_info info{};
   shk_mphf* result = nullptr;
+  volatile uint32_t* abort = nullptr;  // the running worker's flag
+  bool cancelled = false;
 };
+
+// offsets[i] -= base on the device
+__global__ void k_rebase(uint64_t* o, uint64_t n, uint64_t base) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] -= base;
+}
 
 // Device bytes a build holds while it runs: keys staged on the device, three
 // 16-byte fingerprint copies (hashed, partitioned once and twice), the leaf
@@ -60,11 +70,15 @@ struct shk_server {
   std::vector<std::thread> threads;
   uint64_t next_id = 1, in_use = 0, peak = 0, submitted = 0, completed = 0, running = 0;
   bool stop = false;
+  cudaStream_t copy_stream = nullptr;  // copies of submitted device keys
 
   void worker() {
     cudaSetDevice(device);
     cudaStream_t st = nullptr;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    // cancellation flag, read by the build's leaf kernels (host-mapped)
+    uint32_t* flag = nullptr;
+    if (cudaHostAlloc((void**)&flag, sizeof(uint32_t), cudaHostAllocMapped) != cudaSuccess) flag = nullptr;
     for (;;) {
       Request* r = nullptr;
       {
@@ -82,17 +96,30 @@ struct shk_server {
         if (in_use > peak) peak = in_use;
         running++;
         r->info.start_ns = now_ns();
+        if (flag) *(volatile uint32_t*)flag = 0;
+        r->abort = flag;
       }
       shk_keys k;
       k.kind = r->kind;
-      k.on_device = 0;
-      k.data = r->data.data();
-      k.str_offsets = r->offsets.empty() ? nullptr : r->offsets.data();
+      k.on_device = r->d_data != nullptr;
+      k.data = k.on_device ? r->d_data : r->data.data();
+      k.str_offsets = k.on_device ? r->d_offsets : (r->offsets.empty() ? nullptr : r->offsets.data());
       k.n_keys = r->n_keys;
       shk_mphf* m = nullptr;
-      const shk_status s = shk_build(&k, &r->opts, st, &m);
+      shk_status s = shk::no_throw([&] { return shk::build_controlled(&k, &r->opts, st, &m, flag); });
+      if (s != SHK_OK) cudaStreamSynchronize(st);
+      if (r->d_data) cudaFreeAsync(r->d_data, st);
+      if (r->d_offsets) cudaFreeAsync(r->d_offsets, st);
       {
         std::lock_guard<std::mutex> lk(mu);
+        r->abort = nullptr;
+        r->d_data = nullptr;
+        r->d_offsets = nullptr;
+        if (r->cancelled && s == SHK_OK) {  // finished before the flag was seen
+          shk_free(m);
+          m = nullptr;
+          s = SHK_ECANCELLED;
+        }
         r->result = m;
         r->info.status = s;
         r->info.done = 1;
@@ -109,6 +136,7 @@ struct shk_server {
       cv_work.notify_all();
     }
     if (st) cudaStreamDestroy(st);
+    if (flag) cudaFreeHost(flag);
   }
 };
 
@@ -123,6 +151,8 @@ static shk_status server_create(uint64_t hbm_budget_bytes, uint32_t workers, shk
     hbm_budget_bytes = (uint64_t)(free_b * 0.8);
   }
   s->budget = hbm_budget_bytes;
+  if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(SHK_ECUDA, "cudaStreamCreate failed");
   const uint32_t w = workers ? workers : 4;
   shk_server* raw = s.get();
   try {
@@ -142,6 +172,72 @@ extern "C" shk_status shk_server_create(uint64_t hbm_budget_bytes, uint32_t work
   return no_throw([&] { return server_create(hbm_budget_bytes, workers, out); });
 }
 
+// Bytes of a key set as the build stages it on the device.
+static uint64_t key_bytes(const shk_keys* keys) {
+  const uint64_t N = keys->n_keys;
+  if (keys->kind == SHK_KEYS_U64) return N * 8;
+  if (keys->kind == SHK_KEYS_FP128) return N * 16;
+  uint64_t span = 0;
+  if (N) {
+    uint64_t ends[2] = {0, 0};
+    if (keys->on_device) {
+      cudaMemcpy(&ends[0], keys->str_offsets, 8, cudaMemcpyDeviceToHost);
+      cudaMemcpy(&ends[1], keys->str_offsets + N, 8, cudaMemcpyDeviceToHost);
+    } else {
+      ends[0] = keys->str_offsets[0];
+      ends[1] = keys->str_offsets[N];
+    }
+    span = ends[1] - ends[0];
+  }
+  return span + 8 * (N + 1);
+}
+
+// Device keys into the library's pool on the server's device (its current
+// device is set for the copy and restored): u64 and 128-bit keys as they
+// are, string bytes from offsets[0] on with their offsets rebased to 0.
+static shk_status copy_device_keys(shk_server* srv, const shk_keys* keys, Request* r) {
+  int old = 0;
+  SHK_CUDA(cudaGetDevice(&old));
+  SHK_CUDA(cudaSetDevice(srv->device));
+  auto run = [&]() -> shk_status {
+    cudaStream_t cs = srv->copy_stream;
+    const uint64_t N = keys->n_keys;
+    if (keys->kind == SHK_KEYS_STR) {
+      uint64_t ends[2] = {0, 0};
+      if (N) {
+        SHK_CUDA(cudaMemcpyAsync(&ends[0], keys->str_offsets, 8, cudaMemcpyDeviceToHost, cs));
+        SHK_CUDA(cudaMemcpyAsync(&ends[1], keys->str_offsets + N, 8, cudaMemcpyDeviceToHost, cs));
+        SHK_CUDA(cudaStreamSynchronize(cs));
+      }
+      const uint64_t total = ends[1] - ends[0];
+      SHK_CUDA(pool_malloc(&r->d_data, total + 8, cs));
+      SHK_CUDA(pool_malloc((void**)&r->d_offsets, (N + 1) * 8, cs));
+      if (total)
+        SHK_CUDA(cudaMemcpyAsync(r->d_data, (const uint8_t*)keys->data + ends[0], total,
+                                 cudaMemcpyDeviceToDevice, cs));
+      SHK_CUDA(cudaMemcpyAsync(r->d_offsets, keys->str_offsets, (N + 1) * 8, cudaMemcpyDeviceToDevice, cs));
+      if (ends[0]) k_rebase<<<(unsigned)((N + 1 + 255) / 256), 256, 0, cs>>>(r->d_offsets, N + 1, ends[0]);
+      SHK_CUDA(cudaGetLastError());
+    } else {
+      const uint64_t bytes = N * (keys->kind == SHK_KEYS_U64 ? 8 : 16);
+      SHK_CUDA(pool_malloc(&r->d_data, bytes ? bytes : 16, cs));
+      if (bytes) SHK_CUDA(cudaMemcpyAsync(r->d_data, keys->data, bytes, cudaMemcpyDeviceToDevice, cs));
+    }
+    SHK_CUDA(cudaStreamSynchronize(cs));
+    return SHK_OK;
+  };
+  shk_status s = run();
+  if (s != SHK_OK) {
+    cudaStreamSynchronize(srv->copy_stream);
+    if (r->d_data) cudaFreeAsync(r->d_data, srv->copy_stream);
+    if (r->d_offsets) cudaFreeAsync(r->d_offsets, srv->copy_stream);
+    r->d_data = nullptr;
+    r->d_offsets = nullptr;
+  }
+  cudaSetDevice(old);
+  return s;
+}
+
 static shk_status server_submit(shk_server* srv, const shk_keys* keys, const shk_build_opts* opts,
                                 uint64_t* req_id) {
   if (keys->kind != SHK_KEYS_U64 && keys->kind != SHK_KEYS_STR && keys->kind != SHK_KEYS_FP128)
@@ -155,28 +251,24 @@ static shk_status server_submit(shk_server* srv, const shk_keys* keys, const shk
   r->n_keys = N;
   r->opts = *opts;
   r->opts.profile = 0;
-  // copy the keys now: the caller's buffers are only borrowed for this call
-  const cudaMemcpyKind dir = keys->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-  if (keys->kind == SHK_KEYS_STR) {
-    r->offsets.resize(N + 1);
-    if (cudaMemcpy(r->offsets.data(), keys->str_offsets, (N + 1) * 8, dir) != cudaSuccess) {
-      return fail(SHK_ECUDA, "copying string offsets failed");
-    }
+  // copy the keys now: the caller's buffers are only borrowed for this call.
+  // Device keys stay on the device (a copy into the library's pool, made on
+  // the server's copy stream and waited for); host keys are copied on the host.
+  if (keys->on_device) {
+    SHK_TRY(copy_device_keys(srv, keys, r.get()));
+  } else if (keys->kind == SHK_KEYS_STR) {
+    r->offsets.assign(keys->str_offsets, keys->str_offsets + N + 1);
     const uint64_t base = r->offsets[0], total = r->offsets[N] - base;
     r->data.resize(total + 8);
-    if (total && cudaMemcpy(r->data.data(), (const uint8_t*)keys->data + base, total, dir) != cudaSuccess) {
-      return fail(SHK_ECUDA, "copying string keys failed");
-    }
+    if (total) memcpy(r->data.data(), (const uint8_t*)keys->data + base, total);
     for (auto& v : r->offsets) v -= base;
   } else {
     const uint64_t bytes = N * (keys->kind == SHK_KEYS_U64 ? 8 : 16);
     r->data.resize(bytes ? bytes : 8);
-    if (bytes && cudaMemcpy(r->data.data(), keys->data, bytes, dir) != cudaSuccess) {
-      return fail(SHK_ECUDA, "copying keys failed");
-    }
+    if (bytes) memcpy(r->data.data(), keys->data, bytes);
   }
   r->info.n_keys = N;
-  r->info.footprint_bytes = footprint(N, *opts, r->data.size());
+  r->info.footprint_bytes = footprint(N, *opts, key_bytes(keys));
   r->info.submit_ns = now_ns();
   const uint64_t id = [&] {
     std::lock_guard<std::mutex> lk(srv->mu);
@@ -264,7 +356,52 @@ extern "C" void shk_server_destroy(shk_server* srv) {
   for (auto& t : srv->threads) t.join();
   for (auto& kv : srv->all) {
     if (kv.second->result) shk_free(kv.second->result);
+    if (kv.second->d_data) cudaFreeAsync(kv.second->d_data, srv->copy_stream);
+    if (kv.second->d_offsets) cudaFreeAsync(kv.second->d_offsets, srv->copy_stream);
     delete kv.second;
   }
+  if (srv->copy_stream) {
+    cudaStreamSynchronize(srv->copy_stream);
+    cudaStreamDestroy(srv->copy_stream);
+  }
   delete srv;
+}
+
+extern "C" shk_status shk_server_cancel(shk_server* srv, uint64_t req_id) {
+  if (!srv) return fail(SHK_EINVAL, "NULL argument");
+  std::unique_lock<std::mutex> lk(srv->mu);
+  auto it = srv->all.find(req_id);
+  if (it == srv->all.end()) return fail(SHK_EINVAL, "unknown request id");
+  Request* r = it->second;
+  if (r->info.done) return SHK_OK;
+  r->cancelled = true;
+  for (auto q = srv->queue.begin(); q != srv->queue.end(); ++q) {
+    if (*q != r) continue;  // still queued: it never runs
+    srv->queue.erase(q);
+    r->info.done = 1;
+    r->info.status = SHK_ECANCELLED;
+    r->info.finish_ns = now_ns();
+    if (r->d_data) cudaFreeAsync(r->d_data, srv->copy_stream);
+    if (r->d_offsets) cudaFreeAsync(r->d_offsets, srv->copy_stream);
+    r->d_data = nullptr;
+    r->d_offsets = nullptr;
+    srv->completed++;
+    lk.unlock();
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_all();
+    return SHK_OK;
+  }
+  if (r->abort) *r->abort = 1;  // running: its leaf search stops at its next work item
+  return SHK_OK;
+}
+
+extern "C" shk_status shk_build_footprint(const shk_keys* keys, const shk_build_opts* opts,
+                                          uint64_t* bytes) {
+  if (!keys || !opts || !bytes) return fail(SHK_EINVAL, "NULL argument");
+  if (keys->kind == SHK_KEYS_STR && keys->n_keys && !keys->str_offsets)
+    return fail(SHK_EINVAL, "string keys need str_offsets");
+  return no_throw([&] {
+    *bytes = footprint(keys->n_keys, *opts, key_bytes(keys));
+    return SHK_OK;
+  });
 }

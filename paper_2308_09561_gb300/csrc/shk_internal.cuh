@@ -45,6 +45,19 @@ constexpr uint32_t kErrBucketOverflow = 1u << 2;
 constexpr uint32_t kErrRibbon = 1u << 3;
 constexpr uint32_t kErrLeafSize = 1u << 4;
 constexpr uint32_t kErrOrient = 1u << 5;
+constexpr uint32_t kErrTimeout = 1u << 6;    // a build's deadline passed
+constexpr uint32_t kErrCancelled = 1u << 7;  // the abort flag was set
+
+// Device global timer in ns.
+__device__ __forceinline__ uint64_t global_ns() {
+#ifdef __CUDA_ARCH__
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+#else
+  return 0;
+#endif
+}
 
 // Rice parameter of a leaf of m keys (frozen literal table of the format):
 // floor(log2(ln2 * 0.8 (e/2)^m e / sqrt(pi m))), the trial bound of the

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _run(env_extra):
     env = dict(os.environ, **env_extra)
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--ref-sample-keys", "2000"],
+                        "--warmup", "0", "--ref-leaves", "2"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     return [line for line in r.stdout.splitlines() if line.startswith("{")]
@@ -26,7 +26,8 @@ def test_reference_arm_prints_the_contract_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "keys/s" and d["value"] > 0
     assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1
-    assert d["config"]["sample_keys"] == 2000 and d["config"]["leaf_size"] == 48
+    assert d["config"]["workload"] == "mphf_build_1e8_strings_leaf64_bucket2000"
+    assert d["config"]["leaf_size"] == 64 and d["config"]["sample"] == "2 leaves per step"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "keys/s", "h2d_bytes_per_step": 0,

@@ -8,6 +8,8 @@ bijection over all keys.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import pytest
 
@@ -37,6 +39,16 @@ def _dev(keys):
     return torch.from_numpy(np.ascontiguousarray(keys).view(np.int64)).cuda()
 
 
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
 def _bijective(ranks_u64, N):
     return np.array_equal(np.sort(ranks_u64), np.arange(N, dtype=np.uint64))
 
@@ -47,7 +59,7 @@ CASES = [(10000, 32, 2000), (3000, 8, 100), (2500, 24, 500), (777, 40, 2000), (1
 
 
 @pytest.mark.parametrize("N,n,b", CASES)
-@pytest.mark.parametrize("sched", [0, 1])
+@pytest.mark.parametrize("sched", [0, 1, 2])
 def test_build_bytes_equal_oracle(pkg, orc, N, n, b, sched):
     keys = inp.distinct_u64(N, 100 + N)
     m = pkg.shk_build(_dev(keys), n, b, sched=sched)
@@ -326,7 +338,7 @@ RF_CASES = [(10000, 32, 2000), (5000, 24, 800), (3000, 36, 1000), (4000, 48, 200
 
 
 @pytest.mark.parametrize("N,n,b", RF_CASES)
-@pytest.mark.parametrize("sched", [0, 1])
+@pytest.mark.parametrize("sched", [0, 1, 2])
 def test_rotation_fitting_build_bytes_equal_oracle(pkg, orc, N, n, b, sched):
     """Leaf mode 1 (rotation fitting with partial hash calculation)."""
     keys = inp.distinct_u64(N, 400 + N)
@@ -528,3 +540,58 @@ def test_full_leaf_batch(pkg, orc, rf):
     po = np.zeros(len(pick) + 1, np.uint32)
     po[1:] = np.cumsum([sizes[i] for i in pick])
     assert np.array_equal(orc.leaf_search_batch(packed, po, 0, rf=rf)[0], v[pick])
+    # 256 leaves drawn uniformly from the batch (all sizes 40..64): the oracle's
+    # minimal values and masks, stored by tests/golden/make_goldens.py
+    rows = _golden_rows("config3_leaf_sample.txt")
+    assert len(rows) == 256
+    for idx, m, seed, fmask, rv, rfm in rows:
+        i = int(idx)
+        assert sizes[i] == int(m)
+        assert int(v[i]) == (int(rv) if rf else int(seed)), i
+        assert int(f[i]) == int(rfm if rf else fmask, 16), i
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_million_keys_leaf48_full_bytes_equal_oracle(pkg, mode):
+    """The 10^6-key, leaf-48, bucket-2000 workload in the launch the bench
+    times: the SHA-256 of the GPU's serialized MPHF equals that of the
+    oracle's full build (tests/golden/config2_build_digest.txt, written from
+    oracle/ only), plain and rotation-fitting leaves."""
+    import hashlib
+
+    keys = inp.distinct_u64(1_000_000, 2)
+    m = pkg.shk_build(_dev(keys), 48, 2000, leaf_mode=mode)
+    blob = m.serialize()
+    m.close()
+    want = {int(r[0]): (int(r[1]), r[2]) for r in _golden_rows("config2_build_digest.txt")}
+    assert len(blob) == want[mode][0]
+    assert hashlib.sha256(blob).hexdigest() == want[mode][1]
+
+
+def test_strings_1e8_leaf64_rotation_fitting_sampled(pkg, orc):
+    """The workload the bench times: 10^8 strings (lengths 10..50, bytes
+    1..127, stream seed 4), n = 64, b = 2000, rotation fitting, eps = 1.5 %,
+    generated on the device.  Every key ranks bijectively; every bucket's size
+    equals the oracle's; the split codes of 50 random buckets and the values of
+    64 leaves drawn uniformly from them equal the oracle's (oracle/sampled.py)."""
+    import torch
+
+    from oracle.sampled import sampled_parity
+
+    N = 100_000_000
+    dd, do = inp.ascii_strings_torch(N, 4, device="cuda")
+    m = pkg.shk_build(dd, 64, 2000, kind=pkg.SHK_KEYS_STR, str_offsets=do, leaf_mode=pkg.SHK_LEAF_ROTATION,
+                      eps_num=983)
+    blob = m.serialize()
+    ranks = m.query(dd, kind=pkg.SHK_KEYS_STR, str_offsets=do)
+    srt, _ = torch.sort(ranks)
+    assert torch.equal(srt, torch.arange(N, device="cuda", dtype=torch.int64))
+    del srt, ranks
+    m.close()
+    data = dd.cpu().numpy()
+    offs = do.cpu().numpy().view(np.uint64)
+    del dd, do
+    lo, hi = orc.fingerprints_str(data, offs)
+    r = sampled_parity(blob, lo, hi, 64, True, n_buckets=50, n_leaves=64, nthreads=os.cpu_count() or 1)
+    assert r["ok"], r
+    assert r["buckets"] == 50_000 and r["sampled_buckets"] == 50 and r["sampled_leaves"] == 64

@@ -144,3 +144,98 @@ def test_several_threads_waiting_on_one_request(pkg):
         assert errors == [pkg.SHK_EINVAL] * 3
     finally:
         pkg.shk_server_destroy(srv)
+
+
+def test_device_submitted_keys_overlap_on_the_gpu_and_equal_alone(pkg):
+    """Continuous batching: 12 requests submitted as device tensors (kept on
+    the device), 4 workers; the leaf-search kernels of at least two requests
+    are resident at once (their device-time intervals intersect), and every
+    result equals the same build alone."""
+    import torch
+
+    reqs = []
+    for i in range(12):
+        keys = inp.splitmix64_stream_torch(40_000 + i, 150_000 + 20_000 * i, device="cuda")
+        reqs.append((keys, (48, 40)[i % 2]))
+    alone = [pkg.shk_build(k, n, 2000).serialize() for k, n in reqs]
+    srv = pkg.shk_server_create(0, 4)
+    try:
+        ids = [pkg.shk_server_submit(srv, k, n, 2000) for k, n in reqs]
+        spans = []
+        for i, rid in enumerate(ids):
+            m, info = pkg.shk_server_wait(srv, rid)
+            assert info["status"] == 0
+            assert m.serialize() == alone[i]
+            st = m.stats()
+            assert st["leaf_t1_ns"] > st["leaf_t0_ns"] > 0
+            spans.append((st["leaf_t0_ns"], st["leaf_t1_ns"]))
+    finally:
+        pkg.shk_server_destroy(srv)
+    spans.sort()
+    overlaps = sum(1 for a, b in zip(spans, spans[1:]) if b[0] < a[1])
+    assert overlaps >= 1, spans
+    torch.cuda.synchronize()
+
+
+def test_cancel_a_running_and_a_queued_request(pkg):
+    """A running build stops at its next leaf-search work item and its request
+    ends with SHK_ECANCELLED; a queued request never runs; a request
+    submitted afterwards equals the same build alone."""
+    import time
+
+    big = inp.distinct_u64(3_000_000, 41)  # leaf 58: seconds of leaf search
+    small = inp.distinct_u64(20000, 42)
+    want = pkg.shk_build(small, 24, 1000).serialize()
+    srv = pkg.shk_server_create(0, 1)
+    try:
+        r_big = pkg.shk_server_submit(srv, big, 58, 2000)
+        r_q = pkg.shk_server_submit(srv, small, 24, 1000)
+        t0 = time.time()
+        while pkg.shk_server_get_stats(srv)["running"] == 0 and time.time() - t0 < 30:
+            time.sleep(0.005)
+        time.sleep(0.3)  # inside the leaf search
+        pkg.shk_server_cancel(srv, r_q)
+        pkg.shk_server_cancel(srv, r_big)
+        m, info = pkg.shk_server_wait(srv, r_big)
+        assert m is None and info["status"] == pkg.SHK_ECANCELLED
+        assert (info["finish_ns"] - info["start_ns"]) / 1e9 < 5.0
+        m, info = pkg.shk_server_wait(srv, r_q)
+        assert m is None and info["status"] == pkg.SHK_ECANCELLED and info["start_ns"] == 0
+        r_after = pkg.shk_server_submit(srv, small, 24, 1000)
+        assert pkg.shk_server_wait(srv, r_after)[0].serialize() == want
+    finally:
+        pkg.shk_server_destroy(srv)
+
+
+def test_deadline_stops_a_build_then_the_same_build_succeeds(pkg, orc):
+    """A time budget far below the leaf search's time fails the build with
+    SHK_ETIMEOUT (the leaf kernels see the deadline and return); the device
+    stays usable and the same build without a budget equals the oracle."""
+    keys = inp.distinct_u64(400_000, 43)
+    with pytest.raises(pkg.ShkError) as e:
+        pkg.shk_build(keys, 52, 2000, deadline_ms=2)
+    assert e.value.status == pkg.SHK_ETIMEOUT
+    small = inp.distinct_u64(5000, 44)
+    assert pkg.shk_build(small, 20, 1000, deadline_ms=60_000).serialize() == orc.build_mphf(small, n=20, b=1000)
+
+
+@pytest.mark.parametrize("kind,n,mode", [("u64", 48, 0), ("u64", 32, 1), ("str", 64, 1), ("u64", 16, 0)])
+def test_footprint_estimate_covers_the_measured_peak(pkg, kind, n, mode):
+    """The server's admission estimate is at least the device memory a build
+    running alone holds at its peak (pool high watermark plus the result),
+    and not more than four times it."""
+    import torch
+
+    for count in (20_000, 400_000):
+        if kind == "u64":
+            keys = inp.splitmix64_stream_torch(50_000 + count, count, device="cuda")
+            kw = {}
+        else:
+            keys, offs = inp.ascii_strings_torch(count, 45, device="cuda")
+            kw = {"kind": pkg.SHK_KEYS_STR, "str_offsets": offs}
+        torch.cuda.synchronize()
+        est = pkg.shk_build_footprint(keys, n, 2000, leaf_mode=mode, **kw)
+        m = pkg.shk_build(keys, n, 2000, leaf_mode=mode, **kw)
+        peak = m.stats()["device_bytes_peak"]
+        m.close()
+        assert 0 < peak <= est <= 4 * peak + (16 << 20), (count, peak, est)

@@ -94,7 +94,7 @@ MUTANTS = [
      "#define RF_PARTIAL_K 8u", "#define RF_PARTIAL_K 4u",
      lambda o: rf_pins.test_candidate_cells_rotation_and_partial_seed(o, 48)),
     ("rotation fitting: value search starts one candidate late",
-     "for (uint64_t v = start; v < cap; v++) {", "for (uint64_t v = start + 1; v < cap; v++) {",
+     "if (v < start) continue;", "if (v <= start) continue;",
      lambda o: rf_pins.test_rf_value_is_the_minimum(o, 3)),
     ("rotation fitting: first cell rotated the other way",
      "*h0 = (uint32_t)((*h0 + r) % m);", "*h0 = (uint32_t)((*h0 + m - r) % m);",
