@@ -19,7 +19,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libshk_gpu.so")
 
-SHK_OK, SHK_EINVAL, SHK_EDUPKEY, SHK_ENOMEM, SHK_ECUDA, SHK_ESEEDCAP, SHK_ETIMEOUT, SHK_EFORMAT = range(8)
+(SHK_OK, SHK_EINVAL, SHK_EDUPKEY, SHK_ENOMEM, SHK_ECUDA, SHK_ESEEDCAP, SHK_ETIMEOUT, SHK_EFORMAT,
+ SHK_ECANCELLED) = range(9)
 SHK_KEYS_U64, SHK_KEYS_STR, SHK_KEYS_FP128 = 0, 1, 2
 SHK_SCHED_PERSISTENT, SHK_SCHED_PER_BUCKET, SHK_SCHED_SINGLE_LAUNCH = 0, 1, 2
 SHK_LEAF_PLAIN, SHK_LEAF_ROTATION = 0, 1

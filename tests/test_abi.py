@@ -178,3 +178,18 @@ def test_noalloc_binding_rejects_short_or_narrow_outputs_before_any_launch():
         pkg.shk_leaf_search_noalloc(keys.to(torch.int32), off, torch.empty(4, dtype=torch.int64))
     with pytest.raises(ValueError, match="device tensors"):
         pkg.shk_leaf_search_noalloc(keys, off, torch.empty(4, dtype=torch.int64))
+
+
+def test_binding_status_and_enum_constants_match_the_header():
+    """Every SHK_ constant the header's enums define has the same value in the
+    binding."""
+    import paper_2308_09561_gb300 as pkg
+
+    text = open(os.path.join(ROOT, "include", "shk.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    found = 0
+    for m in re.finditer(r"typedef enum \{(.*?)\}", text, flags=re.S):
+        for name, val in re.findall(r"(SHK_\w+)\s*=\s*(\d+)", m.group(1)):
+            assert getattr(pkg, name) == int(val), name
+            found += 1
+    assert found >= 20
