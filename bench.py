@@ -27,7 +27,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # headline workload: 10^8 strings, leaf 64, bucket 2000, rotation fitting
-STR_KEYS, STR_LEAF, STR_BUCKET, STR_SEED, STR_EPS = 100_000_000, 64, 2000, 4, 983
+# (retrieval overhead: the library's default for 128-bit rows, eps = 164 / 2^16)
+STR_KEYS, STR_LEAF, STR_BUCKET, STR_SEED, STR_EPS = 100_000_000, 64, 2000, 4, 0
 WORKLOAD = "mphf_build_1e8_strings_leaf64_bucket2000"
 METRIC = ("MPHF build keys/s (10^8 random strings, leaf 64, bucket 2000, rotation fitting), "
           "leaf seeds tested/s, % integer-issue roofline")
@@ -184,7 +185,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": WORKLOAD, "keys": STR_KEYS, "leaf_size": STR_LEAF, "bucket_size": STR_BUCKET,
-                       "leaf_mode": "rotation fitting", "eps_num": STR_EPS,
+                       "leaf_mode": "rotation fitting", "eps_num": STR_EPS or "library default",
                        "sample": f"{args.ref_leaves} leaves per step"},
             "cpu_baseline": {"value": value, "unit": "keys/s", "cores": threads, "kind": "oracle",
                              "sample": f"per step: the rotation-fitting leaf search of {args.ref_leaves} leaves of "
@@ -194,6 +195,19 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _bits_parts(blob: bytes, count: int) -> dict:
+    """bits/key by section, from the serialized header (16 u64 words: N, n, b,
+    B, shard buckets, eps_num, shards, Rice bits, Elias-Fano widths and high
+    bits, retrieval bits, leaf mode, retrieval row width)."""
+    h = np.frombuffer(blob[:128], dtype="<u8").astype(np.int64)
+    B = int(h[4])
+    ef = (B + 1) * int(h[9]) + int(h[10]) + (B + 1) * int(h[11]) + int(h[12])
+    return {"rice_codes": int(h[8]) / count, "elias_fano": ef / count, "shard_seeds": 8 * int(h[7]) / count,
+            "retrieval": int(h[13]) / count, "header_and_padding": (8 * len(blob) - int(h[8]) - ef - 8 * int(h[7])
+                                                                    - int(h[13])) / count,
+            "retrieval_row_bits": int(h[15]), "retrieval_eps_num": int(h[6]), "shard_buckets": int(h[5])}
 
 
 def _int_issue(pkg):
@@ -420,6 +434,7 @@ def run_ours(args):
                          "steps, outside the step events",
                    "parallelism": f"replicas x{ws}"},
         "bits_per_key": 8 * len(blob) / count,
+        "bits_per_key_parts": _bits_parts(blob, count),
         "bijection_all_keys": bijection,
         "leaf_seeds_per_s": st["leaf_seeds_tested"] / (leaf_ms / 1e3),
         "leaf_candidates_per_s": st["leaf_seeds_min"] / (leaf_ms / 1e3),
@@ -677,7 +692,8 @@ def main():
                     help="serve: largest request (sizes log-uniform from 1e3; 1e7 in the full stream)")
     ap.add_argument("--serve-rf", action="store_true", help="serve: rotation-fitting leaves")
     ap.add_argument("--eps-num", type=int, default=STR_EPS,
-                    help="headline: retrieval overhead eps = eps_num / 65536 (default 983, ~1.5 %%)")
+                    help="headline: retrieval overhead eps = eps_num / 65536 (0: the library default, "
+                         "164 (0.25 %%) for the 128-bit rows of leaf size 64)")
     ap.add_argument("--leafbatch-rf", dest="workload_leafbatch_rf", action="store_true",
                     help="leafbatch: rotation fitting (shk_leaf_search_rf)")
     ap.add_argument("--leaf-mode", default="rf", choices=["rf", "plain"],

@@ -9,7 +9,7 @@
  * bit-mask filter of Sec. 4), the orientation bits of all keys stored in one
  * 1-bit retrieval structure (Sec. 2 Retrieval, Sec. 6).  Every step runs in CUDA
  * kernels on the calling device; the result is bit-identical to the format
- * defined by the project (version SHKRS001).
+ * defined by the project (version SHKRS002).
  *
  * Conventions
  *   - Every function returns an shk_status and never aborts.  On failure a
@@ -174,13 +174,13 @@ shk_status shk_build_stats(const shk_mphf* mphf, shk_stats* out);
 shk_status shk_query(const shk_mphf* mphf, const shk_keys* keys, uint64_t* ranks_out,
                      int out_on_device, void* cuda_stream);
 
-/* shk_serialize -- copy the encoded MPHF (format SHKRS001) into buf (host).
+/* shk_serialize -- copy the encoded MPHF (format SHKRS002) into buf (host).
  * With buf == NULL or cap too small, only *len is set (and SHK_EINVAL is
  * returned if buf was given but too small). */
 shk_status shk_serialize(const shk_mphf* mphf, uint8_t* buf, size_t cap, size_t* len);
 
 /* shk_deserialize -- load a serialized MPHF (host bytes) onto the current
- * device.  SHK_EFORMAT if the bytes are not a well-formed SHKRS001 object. */
+ * device.  SHK_EFORMAT if the bytes are not a well-formed SHKRS002 object. */
 shk_status shk_deserialize(const uint8_t* buf, size_t len, shk_mphf** out);
 
 /* shk_size_bits -- size of the encoded MPHF in bits (header included). */
@@ -316,7 +316,8 @@ shk_status shk_server_cancel(shk_server* srv, uint64_t req_id);
 
 /* shk_build_footprint -- the device bytes the server reserves for a build of
  * these keys with these options (the admission estimate): the keys as
- * staged, 80 bytes per key, 96 per bucket and 8 MiB.  A build that runs
+ * staged, 112 bytes per key (leaf size above 24: 128-bit retrieval rows) or
+ * 96, 96 per bucket and 8 MiB.  A build that runs
  * alone reports its measured peak in shk_stats.device_bytes_peak. */
 shk_status shk_build_footprint(const shk_keys* keys, const shk_build_opts* opts, uint64_t* bytes);
 
@@ -344,7 +345,7 @@ void shk_server_destroy(shk_server* srv);
 shk_status shk_int_issue_rate(uint32_t mix, uint32_t iters, double* rate, double* ms,
                               void* cuda_stream);
 
-/* shk_version -- format version string ("SHKRS001"). */
+/* shk_version -- format version string ("SHKRS002"). */
 const char* shk_version(void);
 
 /* shk_release_memory -- return to the device the working memory the library

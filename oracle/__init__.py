@@ -32,7 +32,7 @@ OK, EINVAL, EDUPKEY, ENOMEM, ESEEDCAP, EFORMAT = 0, 1, 2, 3, 5, 7
 KEYS_U64, KEYS_STR, KEYS_FP128 = 0, 1, 2
 SEED_CAP = 1 << 40
 HEADER_WORDS = 16
-MAGIC = 0x31303053524B4853
+MAGIC = 0x32303053524B4853
 DEFAULT_EPS_NUM = 3277  # epsilon = 3277 / 2^16 ~ 5 %
 
 
@@ -87,10 +87,12 @@ def _load():
             "orc_rf_cells": (None, [u64, u64, u32, vp, vp]),
             "orc_rf_value": (i32, [vp, u32, u64, u64, i32, vp]),
             "orc_orient_mode": (i32, [i32, vp, u32, u64, vp]),
-            "orc_ribbon_shard": (i32, [vp, vp, vp, u64, u32, vp, vp]),
-            "orc_ribbon_rows": (None, [vp, vp, u64, u32, u64, vp, vp]),
-            "orc_shard_slots": (u64, [u64, u32]),
-            "orc_default_shard_buckets": (u32, [u32]),
+            "orc_ribbon_shard": (i32, [vp, vp, vp, u64, u32, u32, vp, vp]),
+            "orc_ribbon_rows": (None, [vp, vp, u64, u32, u64, u32, vp, vp, vp]),
+            "orc_shard_slots": (u64, [u64, u32, u32]),
+            "orc_default_shard_buckets": (u32, [u32, u32]),
+            "orc_default_eps_num": (u32, [u32]),
+            "orc_ribbon_width": (u32, [u32]),
             "orc_build": (i32, [i32, vp, vp, u64, u32, u32, u32, u32, i32, i32, vp, vp]),
             "orc_query": (i32, [vp, u64, vp, vp, u64, vp]),
             "orc_free": (None, [vp]),
@@ -320,47 +322,57 @@ def bucket_splits(lo_sorted, hi_sorted, n: int):
             lm[: nl.value].copy())
 
 
-def shard_slots(keys: int, eps_num: int = DEFAULT_EPS_NUM) -> int:
-    return int(_load().orc_shard_slots(keys, eps_num))
+def shard_slots(keys: int, eps_num: int = DEFAULT_EPS_NUM, w: int = 64) -> int:
+    return int(_load().orc_shard_slots(keys, eps_num, w))
 
 
-def default_shard_buckets(b: int) -> int:
-    return int(_load().orc_default_shard_buckets(b))
+def default_shard_buckets(b: int, w: int = 64) -> int:
+    return int(_load().orc_default_shard_buckets(b, w))
 
 
-def ribbon_rows(lo, hi, seed: int, m: int):
+def ribbon_rows(lo, hi, seed: int, m: int, w: int = 64):
     """(start, coeff) of every key's retrieval row under shard seed `seed` in
-    a shard of m slots."""
+    a shard of m slots of width w; coeff as Python ints of w bits."""
     lo = _u64(lo)
     hi = _u64(hi)
     start = np.empty_like(lo)
-    coeff = np.empty_like(lo)
-    _load().orc_ribbon_rows(_p(lo), _p(hi), lo.size, seed, m, _p(start), _p(coeff))
-    return start, coeff
+    c0 = np.empty_like(lo)
+    c1 = np.empty_like(lo)
+    _load().orc_ribbon_rows(_p(lo), _p(hi), lo.size, seed, m, w, _p(start), _p(c0), _p(c1))
+    return start, [int(a) | (int(b) << 64) for a, b in zip(c0, c1)]
 
 
-def ribbon_shard(lo, hi, f, eps_num: int = DEFAULT_EPS_NUM):
-    """Smallest consistent shard seed and the canonical solution bits."""
+def ribbon_width(n: int) -> int:
+    """Retrieval row width for leaf size n (128 above 24, else 64)."""
+    return int(_load().orc_ribbon_width(n))
+
+
+def default_eps_num(w: int) -> int:
+    return int(_load().orc_default_eps_num(w))
+
+
+def ribbon_shard(lo, hi, f, eps_num: int = DEFAULT_EPS_NUM, w: int = 64):
+    """Smallest consistent shard seed and the canonical solution bits (ribbon
+    width w)."""
     lo = _u64(lo)
     hi = _u64(hi)
     f = np.ascontiguousarray(f, dtype=np.uint8)
-    m = shard_slots(lo.size, eps_num)
+    m = shard_slots(lo.size, eps_num, w)
     sol = np.zeros(max(m, 1), np.uint8)
     seed = ctypes.c_uint32()
-    st = _load().orc_ribbon_shard(_p(lo), _p(hi), _p(f), lo.size, eps_num, ctypes.byref(seed), _p(sol))
+    st = _load().orc_ribbon_shard(_p(lo), _p(hi), _p(f), lo.size, eps_num, w, ctypes.byref(seed), _p(sol))
     if st:
         raise OracleError(st, "ribbon_shard")
     return seed.value, sol[:m].copy()
 
 
 def build_mphf(keys=None, *, kind: int = KEYS_U64, str_data=None, str_offsets=None, fp=None,
-               n: int = 32, b: int = 2000, shard_buckets: int | None = None,
-               eps_num: int = DEFAULT_EPS_NUM, nthreads: int = 0, leaf_mode: int = 0) -> bytes:
+               n: int = 32, b: int = 2000, shard_buckets: int = 0,
+               eps_num: int = 0, nthreads: int = 0, leaf_mode: int = 0) -> bytes:
     """Whole construction -> serialized MPHF bytes.  leaf_mode 0: plain
-    ShockHash leaves; 1: rotation fitting with partial hash calculation."""
+    ShockHash leaves; 1: rotation fitting with partial hash calculation.
+    shard_buckets / eps_num 0: the defaults of the leaf size's ribbon width."""
     lib = _load()
-    if shard_buckets is None:
-        shard_buckets = default_shard_buckets(b)
     offs = None
     if kind == KEYS_U64:
         data = _u64(keys)

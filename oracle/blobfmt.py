@@ -14,7 +14,7 @@ import numpy as np
 
 HEADER = ["magic", "N", "n", "b", "B", "shard_buckets", "eps_num", "num_shards",
           "rice_bits", "efK_l", "efK_hi_bits", "efO_l", "efO_hi_bits", "ribbon_bits",
-          "leaf_mode", "reserved"]
+          "leaf_mode", "ribbon_width"]
 
 
 def _words(nbits):

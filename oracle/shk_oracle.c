@@ -61,7 +61,7 @@ enum { ORC_KEYS_U64 = 0, ORC_KEYS_STR = 1, ORC_KEYS_FP128 = 2 };
 #define ORC_SEED_CAP (1ull << 40)
 #define ORC_RIBBON_SEEDS 256u
 #define ORC_HEADER_WORDS 16u
-#define ORC_MAGIC 0x31303053524B4853ull /* "SHKRS001" */
+#define ORC_MAGIC 0x32303053524B4853ull /* "SHKRS002" */
 
 /* Format constants: salts (hex digits of pi). */
 #define FP_HI_SALT 0x243F6A8885A308D3ull
@@ -69,6 +69,7 @@ enum { ORC_KEYS_U64 = 0, ORC_KEYS_STR = 1, ORC_KEYS_FP128 = 2 };
 #define SPLIT_SALT 0xBE5466CF34E90C6Cull
 #define RET_SALT 0xC0AC29B7C97C50DDull
 #define RET_SALT2 0x3F84D5B5B5470917ull
+#define RET_SALT3 0xA4093822299F31D0ull
 #define STR_SALT_A 0x9216D5D98979FB1Bull
 #define STR_SALT_B 0xD1310BA698DFB5ACull
 #define RF_SALT 0x2FFD72DBD01ADFB7ull
@@ -789,33 +790,52 @@ static void ef_decode_all(const uint64_t* low, const uint64_t* high, uint64_t hb
 
 /* ------------------------------------------------------------------------ */
 /* 1-bit retrieval (Sec. 2 Retrieval; Sec. 6: all f bits go into one          */
-/* retrieval structure).  Reading: a standard ribbon, width 64, sharded by   */
-/* runs of shard_buckets buckets.  Shard slots m = keys + ceil(keys * eps /  */
-/* 2^16) + 63 (0 for an empty shard).  Key equation with shard seed r:        */
+/* retrieval structure; Sec. 8.2: 128-bit words, 64 bits for n <= 24).       */
+/* Reading: a standard ribbon of width w (128 for n > 24, else 64), sharded  */
+/* by runs of shard_buckets buckets.  Shard slots m = keys + ceil(keys * eps */
+/* / 2^16) + w - 1 (0 for an empty shard).  Key equation with shard seed r:  */
 /*   t = mix(hi ^ (RET_SALT + r)), u = mix(lo ^ t),                          */
-/*   start = floor(u * (m - 63) / 2^64), coeff = mix(u ^ RET_SALT2) | 1,      */
-/*   parity(coeff & sol[start .. start + 63]) = f(x).                          */
+/*   start = floor(u * (m - w + 1) / 2^64), coeff bits 0..63 =               */
+/*   mix(u ^ RET_SALT2) | 1, bits 64..127 = mix(u ^ RET_SALT3) (w = 128),     */
+/*   parity(coeff & sol[start .. start + w - 1]) = f(x).                      */
 /* r is the smallest seed in [0, 256) giving a consistent system; the stored */
 /* solution is the unique one that is zero on every non-pivot column, pivots */
 /* being the lowest set column of each echelon row.                          */
 /* ------------------------------------------------------------------------ */
-static uint64_t shard_slots(uint64_t keys, uint32_t eps_num) {
+/* Ribbon width (Sec. 8.2: BuRR with 128-bit words, 64 bits for n <= 24). */
+uint32_t orc_ribbon_width(uint32_t n) { return n > 24 ? 128u : 64u; }
+
+static uint64_t shard_slots(uint64_t keys, uint32_t eps_num, uint32_t w) {
   if (keys == 0) return 0;
-  return keys + (keys * eps_num + 65535) / 65536 + 63;
+  return keys + (keys * eps_num + 65535) / 65536 + (w - 1);
 }
 
-static void ribbon_row(uint64_t lo, uint64_t hi, uint32_t r, uint64_t m, uint64_t* start,
-                       uint64_t* coeff) {
+/* Row of one key: band start in [0, m - w] and a w-bit coefficient with bit
+ * 0 set (w = 64: the low word only). */
+static void ribbon_row(uint64_t lo, uint64_t hi, uint32_t r, uint64_t m, uint32_t w,
+                       uint64_t* start, u128* coeff) {
   uint64_t t = orc_mix64(hi ^ (RET_SALT + r));
   uint64_t u = orc_mix64(lo ^ t);
-  *start = (uint64_t)(((u128)u * (m - 63)) >> 64);
-  *coeff = orc_mix64(u ^ RET_SALT2) | 1ull;
+  *start = (uint64_t)(((u128)u * (m - (w - 1))) >> 64);
+  uint64_t c0 = orc_mix64(u ^ RET_SALT2) | 1ull;
+  uint64_t c1 = w == 128 ? orc_mix64(u ^ RET_SALT3) : 0;
+  *coeff = ((u128)c1 << 64) | c0;
 }
 
 /* The rows of n keys under shard seed r in a shard of m slots (for tests). */
 void orc_ribbon_rows(const uint64_t* lo, const uint64_t* hi, uint64_t n, uint32_t r, uint64_t m,
-                     uint64_t* start, uint64_t* coeff) {
-  for (uint64_t i = 0; i < n; i++) ribbon_row(lo[i], hi[i], r, m, &start[i], &coeff[i]);
+                     uint32_t w, uint64_t* start, uint64_t* coeff_lo, uint64_t* coeff_hi) {
+  for (uint64_t i = 0; i < n; i++) {
+    u128 c;
+    ribbon_row(lo[i], hi[i], r, m, w, &start[i], &c);
+    coeff_lo[i] = (uint64_t)c;
+    coeff_hi[i] = (uint64_t)(c >> 64);
+  }
+}
+
+static unsigned ctz128(u128 v) {
+  uint64_t lo = (uint64_t)v;
+  return lo ? (unsigned)__builtin_ctzll(lo) : 64u + (unsigned)__builtin_ctzll((uint64_t)(v >> 64));
 }
 
 /* Gaussian elimination restricted to the band: a row is reduced by the row
@@ -823,13 +843,14 @@ void orc_ribbon_rows(const uint64_t* lo, const uint64_t* hi, uint64_t n, uint32_
  * vanishes (consistent if its right-hand side vanishes too).  Back
  * substitution then fills pivot columns from the top, free columns = 0. */
 static int ribbon_solve_shard(const uint64_t* lo, const uint64_t* hi, const uint8_t* f,
-                              uint64_t keys, uint64_t m, uint32_t r, uint64_t* rows,
+                              uint64_t keys, uint64_t m, uint32_t w, uint32_t r, u128* rows,
                               uint8_t* rhs, uint8_t* sol) {
-  memset(rows, 0, (size_t)m * 8);
+  memset(rows, 0, (size_t)m * sizeof(u128));
   memset(rhs, 0, (size_t)m);
   for (uint64_t i = 0; i < keys; i++) {
-    uint64_t st, c;
-    ribbon_row(lo[i], hi[i], r, m, &st, &c);
+    uint64_t st;
+    u128 c;
+    ribbon_row(lo[i], hi[i], r, m, w, &st, &c);
     uint8_t b = f[i];
     for (;;) {
       if (rows[st] == 0) {
@@ -843,7 +864,7 @@ static int ribbon_solve_shard(const uint64_t* lo, const uint64_t* hi, const uint
         if (b) return 0;
         break;
       }
-      unsigned tz = (unsigned)__builtin_ctzll(c);
+      unsigned tz = ctz128(c);
       c >>= tz;
       st += tz;
     }
@@ -854,7 +875,7 @@ static int ribbon_solve_shard(const uint64_t* lo, const uint64_t* hi, const uint
       continue;
     }
     uint8_t b = rhs[ii];
-    for (uint32_t j = 1; j < 64; j++)
+    for (uint32_t j = 1; j < w; j++)
       if ((rows[ii] >> j) & 1) b ^= sol[ii + j];
     sol[ii] = b;
   }
@@ -863,13 +884,13 @@ static int ribbon_solve_shard(const uint64_t* lo, const uint64_t* hi, const uint
 
 /* Solve one shard: smallest consistent seed, canonical solution bits. */
 int orc_ribbon_shard(const uint64_t* lo, const uint64_t* hi, const uint8_t* f, uint64_t keys,
-                     uint32_t eps_num, uint32_t* seed_out, uint8_t* sol /* shard_slots */) {
-  uint64_t m = shard_slots(keys, eps_num);
+                     uint32_t eps_num, uint32_t w, uint32_t* seed_out, uint8_t* sol /* shard_slots */) {
+  uint64_t m = shard_slots(keys, eps_num, w);
   if (m == 0) {
     *seed_out = 0;
     return ORC_OK;
   }
-  uint64_t* rows = (uint64_t*)malloc((size_t)m * 8);
+  u128* rows = (u128*)malloc((size_t)m * sizeof(u128));
   uint8_t* rhs = (uint8_t*)malloc((size_t)m);
   if (!rows || !rhs) {
     free(rows);
@@ -878,7 +899,7 @@ int orc_ribbon_shard(const uint64_t* lo, const uint64_t* hi, const uint8_t* f, u
   }
   int st = ORC_ESEEDCAP;
   for (uint32_t r = 0; r < ORC_RIBBON_SEEDS; r++)
-    if (ribbon_solve_shard(lo, hi, f, keys, m, r, rows, rhs, sol)) {
+    if (ribbon_solve_shard(lo, hi, f, keys, m, w, r, rows, rhs, sol)) {
       *seed_out = r;
       st = ORC_OK;
       break;
@@ -888,7 +909,9 @@ int orc_ribbon_shard(const uint64_t* lo, const uint64_t* hi, const uint8_t* f, u
   return st;
 }
 
-uint64_t orc_shard_slots(uint64_t keys, uint32_t eps_num) { return shard_slots(keys, eps_num); }
+uint64_t orc_shard_slots(uint64_t keys, uint32_t eps_num, uint32_t w) {
+  return shard_slots(keys, eps_num, w);
+}
 
 /* ------------------------------------------------------------------------ */
 /* Whole build.                                                              */
@@ -906,19 +929,26 @@ static void put_words(uint8_t* out, uint64_t* pos_words, const uint64_t* w, uint
   *pos_words += nwords;
 }
 
-uint32_t orc_default_shard_buckets(uint32_t b) {
-  uint32_t s = 8192u / b;
+/* Retrieval defaults per ribbon width: shards of about 8,192 keys and
+ * eps = 5 % (w = 64), 16,384 keys and eps = 0.25 % (w = 128). */
+uint32_t orc_default_shard_buckets(uint32_t b, uint32_t w) {
+  uint32_t s = (w == 128 ? 16384u : 8192u) / b;
   return s ? s : 1u;
 }
+
+uint32_t orc_default_eps_num(uint32_t w) { return w == 128 ? 164u : 3277u; }
 
 int orc_build(int kind, const void* data, const uint64_t* offs, uint64_t N, uint32_t n,
               uint32_t b, uint32_t shard_buckets, uint32_t eps_num, int nthreads, int leaf_mode,
               uint8_t** out, uint64_t* out_len) {
   *out = NULL;
   *out_len = 0;
-  if (n < 2 || n > ORC_MAX_LEAF || b < n || b > ORC_MAX_BUCKET_SIZE || shard_buckets == 0 ||
-      N >= (1ull << 32) || (leaf_mode != 0 && leaf_mode != 1))
+  if (n < 2 || n > ORC_MAX_LEAF || b < n || b > ORC_MAX_BUCKET_SIZE || N >= (1ull << 32) ||
+      (leaf_mode != 0 && leaf_mode != 1))
     return ORC_EINVAL;
+  const uint32_t rw_bits = orc_ribbon_width(n);
+  if (shard_buckets == 0) shard_buckets = orc_default_shard_buckets(b, rw_bits);
+  if (eps_num == 0) eps_num = orc_default_eps_num(rw_bits);
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -1014,7 +1044,7 @@ int orc_build(int kind, const void* data, const uint64_t* offs, uint64_t N, uint
   /* retrieval shards */
   for (uint64_t s = 0; s < num_shards; s++) {
     uint64_t b0 = s * shard_buckets, b1 = b0 + shard_buckets < B ? b0 + shard_buckets : B;
-    shard_off[s + 1] = shard_off[s] + shard_slots(K[b1] - K[b0], eps_num);
+    shard_off[s + 1] = shard_off[s] + shard_slots(K[b1] - K[b0], eps_num, rw_bits);
   }
   solbits = (uint8_t*)calloc((size_t)shard_off[num_shards] + 1, 1);
   if (!solbits) {
@@ -1026,7 +1056,7 @@ int orc_build(int kind, const void* data, const uint64_t* offs, uint64_t N, uint
     uint64_t b0 = (uint64_t)s * shard_buckets;
     uint64_t b1 = b0 + shard_buckets < B ? b0 + shard_buckets : B;
     uint64_t k0 = K[b0], keys = K[b1] - K[b0];
-    int st = orc_ribbon_shard(lo + k0, hi + k0, f + k0, keys, eps_num, &shard_seed[s],
+    int st = orc_ribbon_shard(lo + k0, hi + k0, f + k0, keys, eps_num, rw_bits, &shard_seed[s],
                               solbits + shard_off[s]);
     if (st != ORC_OK) {
 #pragma omp critical
@@ -1047,7 +1077,7 @@ int orc_build(int kind, const void* data, const uint64_t* offs, uint64_t N, uint
     }
     uint64_t hdr[ORC_HEADER_WORDS] = {ORC_MAGIC, N, n, b, B, shard_buckets, eps_num, num_shards,
                                       rice.nbits, lK, kh.nbits, lO, oh.nbits, rib_bits,
-                                      (uint64_t)leaf_mode, 0};
+                                      (uint64_t)leaf_mode, rw_bits};
     uint64_t pw = 0;
     put_words(blob, &pw, hdr, ORC_HEADER_WORDS);
     put_words(blob, &pw, rice.w, w_rice);
@@ -1096,7 +1126,7 @@ done:
 /* h_{s,f(x)}(x)).  Decodes the tree from the bucket's Rice stream.          */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  uint64_t N, n, b, B, shard_buckets, eps_num, num_shards, leaf_mode;
+  uint64_t N, n, b, B, shard_buckets, eps_num, num_shards, leaf_mode, width;
   const uint64_t* rice;
   const uint8_t* seeds;
   const uint64_t* rib;
@@ -1140,11 +1170,12 @@ static uint64_t query_one(const mphf_view_t* v, uint64_t lo, uint64_t hi) {
     uint64_t sh = bkt / v->shard_buckets;
     uint64_t b0 = sh * v->shard_buckets;
     uint64_t b1 = b0 + v->shard_buckets < v->B ? b0 + v->shard_buckets : v->B;
-    uint64_t ms = shard_slots(v->K[b1] - v->K[b0], (uint32_t)v->eps_num);
-    uint64_t st, c;
-    ribbon_row(lo, hi, v->seeds[sh], ms, &st, &c);
+    uint64_t ms = shard_slots(v->K[b1] - v->K[b0], (uint32_t)v->eps_num, (uint32_t)v->width);
+    uint64_t st;
+    u128 c;
+    ribbon_row(lo, hi, v->seeds[sh], ms, (uint32_t)v->width, &st, &c);
     int bit = 0;
-    for (uint32_t j = 0; j < 64; j++)
+    for (uint32_t j = 0; j < v->width; j++)
       if ((c >> j) & 1) bit ^= get_bit(v->rib, v->shard_off[sh] + st + j);
     local = bit ? h1 : h0;
   }
@@ -1165,7 +1196,9 @@ int orc_query(const uint8_t* blob, uint64_t len, const uint64_t* lo, const uint6
   v.eps_num = h[6];
   v.num_shards = h[7];
   v.leaf_mode = h[14];
-  if (v.leaf_mode > 1) return ORC_EFORMAT;
+  v.width = h[15];
+  if (v.leaf_mode > 1 || v.n < 2 || v.n > ORC_MAX_LEAF || v.width != orc_ribbon_width((uint32_t)v.n))
+    return ORC_EFORMAT;
   uint64_t rice_bits = h[8], lK = h[9], khb = h[10], lO = h[11], ohb = h[12], rib = h[13];
   if (v.N == 0) return nq == 0 ? ORC_OK : ORC_EINVAL;
   uint64_t pw = ORC_HEADER_WORDS;
@@ -1199,7 +1232,8 @@ int orc_query(const uint8_t* blob, uint64_t len, const uint64_t* lo, const uint6
   for (uint64_t s = 0; s < v.num_shards; s++) {
     uint64_t b0 = s * v.shard_buckets;
     uint64_t b1 = b0 + v.shard_buckets < v.B ? b0 + v.shard_buckets : v.B;
-    v.shard_off[s + 1] = v.shard_off[s] + shard_slots(v.K[b1] - v.K[b0], (uint32_t)v.eps_num);
+    v.shard_off[s + 1] =
+        v.shard_off[s] + shard_slots(v.K[b1] - v.K[b0], (uint32_t)v.eps_num, (uint32_t)v.width);
   }
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < (int64_t)nq; i++) ranks[i] = query_one(&v, lo[i], hi[i]);

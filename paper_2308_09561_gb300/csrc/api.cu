@@ -264,8 +264,9 @@ shk_status build_controlled(const shk_keys* keys, const shk_build_opts* o, cudaS
   if (o->sched > SHK_SCHED_SINGLE_LAUNCH) return fail(SHK_EINVAL, "unknown schedule");
   if (o->leaf_mode > SHK_LEAF_ROTATION) return fail(SHK_EINVAL, "unknown leaf mode");
   const uint32_t rf = o->leaf_mode;
-  const uint32_t S = o->shard_buckets ? o->shard_buckets : std::max(1u, 8192u / b);
-  const uint32_t eps = o->eps_num ? o->eps_num : kDefaultEpsNum;
+  const uint32_t rw = ribbon_width(n);  // retrieval row width
+  const uint32_t S = o->shard_buckets ? o->shard_buckets : default_shard_buckets(b, rw);
+  const uint32_t eps = o->eps_num ? o->eps_num : default_eps_num(rw);
   Ctx c(st);
   SHK_TRY(init_ctx(c));
   // leaf kernel configuration: the autotuner's choice for this leaf size,
@@ -408,7 +409,7 @@ shk_status build_controlled(const shk_keys* keys, const shk_build_opts* o, cudaS
   SHK_TRY(c.arena.alloc(&slots, num_shards));
   SHK_TRY(c.arena.alloc(&shard_off, num_shards + 1));
   SHK_TRY(c.arena.alloc(&max_sk, 1, true));
-  SHK_TRY(launch_shard_slots(c, K, B, S, eps, num_shards, slots));
+  SHK_TRY(launch_shard_slots(c, K, B, S, eps, rw, num_shards, slots));
   SHK_TRY((exclusive_scan<uint64_t, uint64_t>(c, slots, num_shards, shard_off)));
   SHK_TRY(launch_max_shard_keys(c, K, B, S, num_shards, max_sk));
   uint64_t h_rice_bits = 0, h_rib_bits = 0;
@@ -429,7 +430,7 @@ shk_status build_controlled(const shk_keys* keys, const shk_build_opts* o, cudaS
   const uint32_t lK = ef_low_bits(N, B + 1), lO = ef_low_bits(h_rice_bits, B + 1);
   const uint64_t hdr[kHeaderWords] = {kMagic, N, n, b, B, S, eps, num_shards, h_rice_bits, lK,
                                       (N >> lK) + B + 1, lO, (h_rice_bits >> lO) + B + 1,
-                                      h_rib_bits, rf, 0};
+                                      h_rib_bits, rf, rw};
   memcpy(m->hdr, hdr, sizeof hdr);
   layout(m);
   shk_status rs = SHK_OK;
@@ -454,8 +455,8 @@ shk_status build_controlled(const shk_keys* keys, const shk_build_opts* o, cudaS
   }
   const int t6 = pt.mark();
   if (rs == SHK_OK)
-    rs = launch_ribbon(c, llo, lhi, f, K, B, S, eps, num_shards, shard_off,
-                       (uint32_t)shard_slots(h_max_sk, eps), m->d_blob + m->off_rib,
+    rs = launch_ribbon(c, llo, lhi, f, K, B, S, eps, rw, num_shards, shard_off,
+                       (uint32_t)shard_slots(h_max_sk, eps, rw), h_rib_bits, N, m->d_blob + m->off_rib,
                        (uint8_t*)(m->d_blob + m->off_seed), err);
   const int t7 = pt.mark();
   if (rs == SHK_OK) {
@@ -515,7 +516,7 @@ using namespace shk;
 
 extern "C" const char* shk_last_error(void) { return g_last_error.c_str(); }
 
-extern "C" const char* shk_version(void) { return "SHKRS001"; }
+extern "C" const char* shk_version(void) { return "SHKRS002"; }
 
 extern "C" void shk_release_memory(void) {
   std::lock_guard<std::mutex> lk(g_pool_mu);
@@ -566,14 +567,14 @@ static shk_status deserialize_impl(const uint8_t* buf, size_t len, shk_mphf** ou
             h[7] == (B + S - 1) / S && h[9] < 64 && h[11] < 64 && h[9] == ef_low_bits(N, B + 1) &&
             h[10] == (N >> h[9]) + B + 1 && h[11] == ef_low_bits(h[8], B + 1) &&
             h[12] == (h[8] >> h[11]) + B + 1 && h[8] < (1ull << 48) && h[13] < (1ull << 48) &&
-            h[14] <= 1 && h[15] == 0;
+            h[14] <= 1 && h[15] == ribbon_width((uint32_t)n);
   if (ok) {
     layout(m);
     ok = m->words * 8 == len;
   }
   if (!ok) {
     delete m;
-    return fail(SHK_EFORMAT, "not a well-formed SHKRS001 object");
+    return fail(SHK_EFORMAT, "not a well-formed SHKRS002 object");
   }
   Ctx c(nullptr);
   shk_status st = init_ctx(c);
@@ -600,7 +601,7 @@ static shk_status deserialize_impl(const uint8_t* buf, size_t len, shk_mphf** ou
     if (h_bad) return fail(SHK_EFORMAT, "inconsistent bucket index");
     uint64_t* slots;
     SHK_TRY(c.arena.alloc(&slots, h[7]));
-    SHK_TRY(launch_shard_slots(c, m->d_K, B, (uint32_t)S, (uint32_t)h[6], h[7], slots));
+    SHK_TRY(launch_shard_slots(c, m->d_K, B, (uint32_t)S, (uint32_t)h[6], (uint32_t)h[15], h[7], slots));
     SHK_TRY((exclusive_scan<uint64_t, uint64_t>(c, slots, h[7], m->d_shard_off)));
     SHK_CUDA(cudaStreamSynchronize(c.stream));
     return SHK_OK;

@@ -150,11 +150,14 @@ shk_status launch_validate_index(Ctx& c, const uint32_t* K, const uint64_t* O, u
                                  uint64_t N, uint64_t rice_bits, uint32_t* bad);
 // a8
 shk_status launch_shard_slots(Ctx& c, const uint32_t* K, uint64_t B, uint32_t S, uint32_t eps_num,
-                              uint64_t num_shards, uint64_t* slots);
+                              uint32_t w, uint64_t num_shards, uint64_t* slots);
+// w = 64 or 128; total_slots = all shards' slots, n_keys = all keys (the
+// 128-bit solver's global scratch)
 shk_status launch_ribbon(Ctx& c, const uint64_t* lo, const uint64_t* hi, const uint8_t* f,
-                         const uint32_t* K, uint64_t B, uint32_t S, uint32_t eps_num,
+                         const uint32_t* K, uint64_t B, uint32_t S, uint32_t eps_num, uint32_t w,
                          uint64_t num_shards, const uint64_t* shard_off, uint32_t max_shard_slots,
-                         uint64_t* sol_words, uint8_t* seeds, uint32_t* err);
+                         uint64_t total_slots, uint64_t n_keys, uint64_t* sol_words, uint8_t* seeds,
+                         uint32_t* err);
 shk_status launch_max_shard_keys(Ctx& c, const uint32_t* K, uint64_t B, uint32_t S,
                                  uint64_t num_shards, uint32_t* out_max);
 // query

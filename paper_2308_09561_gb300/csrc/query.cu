@@ -16,7 +16,7 @@ struct QueryView {
   const uint64_t* O;
   const uint64_t* shard_off;
   uint64_t B;
-  uint32_t n, S, eps_num, leaf_mode;
+  uint32_t n, S, eps_num, leaf_mode, w;
 };
 
 __device__ __forceinline__ uint64_t window64(const uint64_t* w, uint64_t nwords, uint64_t p) {
@@ -25,6 +25,21 @@ __device__ __forceinline__ uint64_t window64(const uint64_t* w, uint64_t nwords,
   uint64_t v = i < nwords ? w[i] >> sh : 0;
   if (sh && i + 1 < nwords) v |= w[i + 1] << (64 - sh);
   return v;
+}
+
+// Retrieval parity of a key: coefficient & solution window (w bits from
+// start) over GF(2).
+__device__ __forceinline__ uint32_t retrieve_bit(const QueryView& q, uint64_t b, uint64_t lo,
+                                                 uint64_t hi) {
+  const uint64_t sh = b / q.S;
+  const uint64_t b0 = sh * q.S, b1 = b0 + q.S < q.B ? b0 + q.S : q.B;
+  const uint64_t ms = shard_slots(q.K[b1] - q.K[b0], q.eps_num, q.w);
+  uint64_t st, c0, c1;
+  ribbon_row(lo, hi, q.seeds[sh], ms, q.w, &st, &c0, &c1);
+  const uint64_t p = q.shard_off[sh] + st;
+  uint32_t par = __popcll(window64(q.rib, q.rib_words, p) & c0);
+  if (q.w == 128) par += __popcll(window64(q.rib, q.rib_words, p + 64) & c1);
+  return par & 1u;
 }
 
 __device__ __forceinline__ uint64_t rice_next(const QueryView& q, uint64_t* pos, uint32_t k) {
@@ -89,13 +104,7 @@ __device__ uint64_t query_one(const QueryView& q, uint64_t lo, uint64_t hi) {
     const uint64_t seed = rice_next(q, &pos, rice_k_leaf(m));
     uint32_t h0, h1;
     value_cells(q.leaf_mode, lo, seed, m, &h0, &h1);
-    const uint64_t sh = b / q.S;
-    const uint64_t b0 = sh * q.S, b1 = b0 + q.S < q.B ? b0 + q.S : q.B;
-    const uint64_t ms = shard_slots(q.K[b1] - q.K[b0], q.eps_num);
-    uint64_t st, cf;
-    ribbon_row(lo, hi, q.seeds[sh], ms, &st, &cf);
-    const uint64_t win = window64(q.rib, q.rib_words, q.shard_off[sh] + st);
-    local = (__popcll(win & cf) & 1) ? h1 : h0;
+    local = retrieve_bit(q, b, lo, hi) ? h1 : h0;
   }
   return q.K[b] + offset + local;
 }
@@ -168,13 +177,7 @@ __device__ uint64_t query_one_indexed(const QueryView& q, const QNode* __restric
   if (m >= 2) {
     uint32_t h0, h1;
     value_cells(q.leaf_mode, lo, nodes[node].seed, m, &h0, &h1);
-    const uint64_t sh = b / q.S;
-    const uint64_t b0 = sh * q.S, b1 = b0 + q.S < q.B ? b0 + q.S : q.B;
-    const uint64_t ms = shard_slots(q.K[b1] - q.K[b0], q.eps_num);
-    uint64_t st, cf;
-    ribbon_row(lo, hi, q.seeds[sh], ms, &st, &cf);
-    const uint64_t win = window64(q.rib, q.rib_words, q.shard_off[sh] + st);
-    local = (__popcll(win & cf) & 1) ? h1 : h0;
+    local = retrieve_bit(q, b, lo, hi) ? h1 : h0;
   }
   return q.K[b] + offset + local;
 }
@@ -202,6 +205,7 @@ static QueryView query_view(const shk_mphf* mp) {
   q.S = (uint32_t)mp->hdr[5];
   q.eps_num = (uint32_t)mp->hdr[6];
   q.leaf_mode = (uint32_t)mp->hdr[14];
+  q.w = (uint32_t)mp->hdr[15];
   return q;
 }
 

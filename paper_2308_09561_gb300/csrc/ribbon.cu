@@ -1,7 +1,8 @@
 // ribbon.cu -- 1-bit retrieval of the orientation bits of all keys (paper
 // Sec. 2 Retrieval: the value is the parity of a hashed row with a segment of
 // a solution table; the table solves a nearly diagonal linear system).  A
-// standard ribbon of width 64, sharded by runs of buckets; one CTA per shard.
+// standard ribbon of width 64 (leaf size n <= 24) or 128 (n > 24; Sec. 8.2's
+// 128-bit words), sharded by runs of buckets; one CTA per shard.
 //
 // Elimination: each key's row (start, 64-bit coefficient with bit 0 set) is
 // reduced by the row stored at its lowest set column until it reaches a free
@@ -75,17 +76,17 @@ __device__ __forceinline__ int eliminate_list(uint64_t* rows, uint8_t* rhs, uint
 }
 
 __global__ void k_shard_slots(const uint32_t* K, uint64_t B, uint32_t S, uint32_t eps_num,
-                              uint64_t num_shards, uint64_t* slots) {
+                              uint32_t w, uint64_t num_shards, uint64_t* slots) {
   const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= num_shards) return;
   const uint64_t b0 = s * S, b1 = b0 + S < B ? b0 + S : B;
-  slots[s] = shard_slots(K[b1] - K[b0], eps_num);
+  slots[s] = shard_slots(K[b1] - K[b0], eps_num, w);
 }
 
 shk_status launch_shard_slots(Ctx& c, const uint32_t* K, uint64_t B, uint32_t S, uint32_t eps_num,
-                              uint64_t num_shards, uint64_t* slots) {
+                              uint32_t w, uint64_t num_shards, uint64_t* slots) {
   if (num_shards == 0) return SHK_OK;
-  k_shard_slots<<<(unsigned)((num_shards + 255) / 256), 256, 0, c.stream>>>(K, B, S, eps_num,
+  k_shard_slots<<<(unsigned)((num_shards + 255) / 256), 256, 0, c.stream>>>(K, B, S, eps_num, w,
                                                                             num_shards, slots);
   c.launches++;
   SHK_CUDA(cudaGetLastError());
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kRibbonThreads)
   const uint64_t sh = blockIdx.x;
   const uint64_t b0 = sh * S, b1 = b0 + S < B ? b0 + S : B;
   const uint32_t k0 = K[b0], keys = K[b1] - K[b0];
-  const uint64_t m = shard_slots(keys, eps_num);
+  const uint64_t m = shard_slots(keys, eps_num, 64);
   if (m == 0) {
     if (threadIdx.x == 0) seeds[sh] = 0;
     return;
@@ -155,8 +156,8 @@ __global__ void __launch_bounds__(kRibbonThreads)
     if (PRE) {
       // rows of this seed, listed by the region of their start slot
       for (uint32_t i = threadIdx.x; i < keys; i += kRibbonThreads) {
-        uint64_t st, cf;
-        ribbon_row(lo[k0 + i], hi[k0 + i], r, m, &st, &cf);
+        uint64_t st, cf, c1;
+        ribbon_row(lo[k0 + i], hi[k0 + i], r, m, 64, &st, &cf, &c1);
         pcoef[i] = cf;
         pstart[i] = (uint32_t)st;
         pbit[i] = f[k0 + i];
@@ -232,8 +233,8 @@ __global__ void __launch_bounds__(kRibbonThreads)
       // without row precomputation: one thread over the whole table
       int ok = 1;
       for (uint32_t i = 0; i < keys && ok; i++) {
-        uint64_t st64, cf;
-        ribbon_row(lo[k0 + i], hi[k0 + i], r, m, &st64, &cf);
+        uint64_t st64, cf, c1;
+        ribbon_row(lo[k0 + i], hi[k0 + i], r, m, 64, &st64, &cf, &c1);
         uint32_t st = (uint32_t)st64;
         uint8_t bv = f[k0 + i];
         if (eliminate(rows, rhs, &st, &cf, &bv, 0xFFFFFFFFu) == 0) ok = 0;
@@ -343,11 +344,238 @@ __global__ void __launch_bounds__(kRibbonThreads)
   }
 }
 
+// ---------------------------------------------------------------------------
+// 128-bit rows (leaf size n > 24).  At the default shard size (about 16,400
+// keys) a shard's band (16 bytes of row and 1 byte of right-hand side per
+// slot) does not fit shared memory, so the band and the per-key rows live in
+// global scratch indexed by global slot / key; a shard's working set (~0.7 MB)
+// stays in L1/L2.  The elimination is the region-parallel one of k_ribbon:
+// lane 0 of warp g eliminates the rows that start in region g, rows that step
+// past their region are parked and continue in rounds through the following
+// regions, and thread 0 finishes any rows still parked.
+// ---------------------------------------------------------------------------
+struct Band128 {
+  uint64_t* lo;  // row bits 0..63 at its pivot slot (0: the slot is free)
+  uint64_t* hi;  // row bits 64..127
+  uint8_t* rhs;
+};
+struct Rows128 {  // per key, reduced state while it is parked
+  uint64_t* lo;
+  uint64_t* hi;
+  uint32_t* start;
+  uint32_t* list;  // keys by region of their start
+  uint8_t* bit;
+};
+
+__device__ __forceinline__ int eliminate128(const Band128& bd, uint32_t* st, uint64_t* clo,
+                                            uint64_t* chi, uint8_t* bv, uint32_t limit) {
+  uint32_t s = *st;
+  uint64_t lo = *clo, hi = *chi;
+  uint8_t b = *bv;
+  for (;;) {
+    if (s >= limit) {
+      *st = s;
+      *clo = lo;
+      *chi = hi;
+      *bv = b;
+      return 2;
+    }
+    const uint64_t rl = bd.lo[s];
+    if (rl == 0) {  // a stored row has bit 0 set, so 0 marks a free slot
+      bd.lo[s] = lo;
+      bd.hi[s] = hi;
+      bd.rhs[s] = b;
+      return 1;
+    }
+    lo ^= rl;
+    hi ^= bd.hi[s];
+    b ^= bd.rhs[s];
+    if ((lo | hi) == 0) return b ? 0 : 1;
+    // bit 0 is now clear: shift the row to its next set bit (1 <= tz <= 127)
+    const uint32_t tz = lo ? ctz64(lo) : 64u + ctz64(hi);
+    if (tz >= 64) {
+      lo = hi >> (tz - 64);
+      hi = 0;
+    } else {
+      lo = (lo >> tz) | (hi << (64 - tz));
+      hi >>= tz;
+    }
+    s += tz;
+  }
+}
+
+template <class Park>
+__device__ __forceinline__ int eliminate_list128(const Band128& bd, const Rows128& rw, uint32_t t0,
+                                                 uint32_t t1, uint32_t limit, Park park) {
+  for (uint32_t t = t0; t < t1; t++) {
+    const uint32_t i = rw.list[t];
+    uint32_t st = rw.start[i];
+    uint64_t lo = rw.lo[i], hi = rw.hi[i];
+    uint8_t bv = rw.bit[i];
+    const int res = eliminate128(bd, &st, &lo, &hi, &bv, limit);
+    if (res == 0) return 0;
+    if (res == 2) {
+      rw.start[i] = st;
+      rw.lo[i] = lo;
+      rw.hi[i] = hi;
+      rw.bit[i] = bv;
+      park(i);
+    }
+  }
+  return 1;
+}
+
+__global__ void __launch_bounds__(kRibbonThreads)
+    k_ribbon128(const uint64_t* __restrict__ lo, const uint64_t* __restrict__ hi,
+                const uint8_t* __restrict__ f, const uint32_t* __restrict__ K, uint64_t B, uint32_t S,
+                uint32_t eps_num, const uint64_t* __restrict__ shard_off, Band128 band, Rows128 rows,
+                uint64_t* sol_words, uint8_t* seeds, uint32_t* err) {
+  const uint64_t sh = blockIdx.x;
+  const uint64_t b0 = sh * S, b1 = b0 + S < B ? b0 + S : B;
+  const uint32_t k0 = K[b0], keys = K[b1] - K[b0];
+  const uint64_t m = shard_slots(keys, eps_num, 128);
+  if (m == 0) {
+    if (threadIdx.x == 0) seeds[sh] = 0;
+    return;
+  }
+  const uint64_t base = shard_off[sh];
+  const Band128 bd{band.lo + base, band.hi + base, band.rhs + base};
+  const Rows128 rw{rows.lo + k0, rows.hi + k0, rows.start + k0, rows.list + k0, rows.bit + k0};
+  __shared__ int ok_s;
+  __shared__ uint32_t seed_s;
+  __shared__ uint32_t rbase[kRegions + 1], rfill[kRegions], rpark[kRegions];
+  const uint32_t w = (uint32_t)((m + kRegions - 1) / kRegions);  // region width in slots
+  for (uint32_t r = 0; r < kRibbonSeeds; r++) {
+    for (uint64_t i = threadIdx.x; i < m; i += kRibbonThreads) bd.lo[i] = 0;
+    if (threadIdx.x < kRegions) rfill[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+      ok_s = 1;
+      seed_s = r;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < keys; i += kRibbonThreads) {
+      uint64_t st, c0, c1;
+      ribbon_row(lo[k0 + i], hi[k0 + i], r, m, 128, &st, &c0, &c1);
+      rw.lo[i] = c0;
+      rw.hi[i] = c1;
+      rw.start[i] = (uint32_t)st;
+      rw.bit[i] = f[k0 + i];
+      atomicAdd(&rfill[(uint32_t)st / w], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const uint32_t lane = threadIdx.x, c = rfill[lane];
+      uint32_t x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+      }
+      rbase[lane] = x - c;
+      if (lane == 31) rbase[kRegions] = x;
+      rfill[lane] = x - c;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < keys; i += kRibbonThreads)
+      rw.list[atomicAdd(&rfill[rw.start[i] / w], 1u)] = i;
+    __syncthreads();
+    // phase 1: every region's own rows, in parallel
+    if ((threadIdx.x & 31) == 0) {
+      const uint32_t g = threadIdx.x >> 5;
+      const uint32_t r1 = (g + 1) * w < m ? (g + 1) * w : (uint32_t)m;
+      const uint32_t t0 = rbase[g], t1 = rbase[g + 1];
+      uint32_t np = t0;
+      const int ok = eliminate_list128(bd, rw, t0, t1, r1, [&](uint32_t i) { rw.list[np++] = i; });
+      rpark[g] = np - t0;
+      if (!ok) ok_s = 0;
+    }
+    __syncthreads();
+    // phase 2: parked rows continue through the following regions in rounds
+    // (in round t region g's rows walk region g + 1 + t; no two warps share a
+    // region in a round), then thread 0 finishes what is left
+    const uint32_t g = threadIdx.x >> 5;
+    const bool leader = (threadIdx.x & 31) == 0;
+    int pending = __syncthreads_or(leader && rpark[g] != 0);
+    for (uint32_t round = 0; pending && ok_s && round < kRegions; round++) {
+      if (leader && rpark[g] != 0) {
+        const uint32_t end = g + 2 + round;
+        const uint32_t lim = end < kRegions ? end * w : 0xFFFFFFFFu;
+        uint32_t keep = 0;
+        const int ok = eliminate_list128(bd, rw, rbase[g], rbase[g] + rpark[g], lim,
+                                         [&](uint32_t i) { rw.list[rbase[g] + keep++] = i; });
+        rpark[g] = keep;
+        if (!ok) ok_s = 0;
+      }
+      pending = __syncthreads_or(leader && rpark[g] != 0);
+    }
+    if (threadIdx.x == 0 && ok_s && pending) {
+      int ok = 1;
+      for (uint32_t h = 0; h < kRegions && ok; h++)
+        ok = eliminate_list128(bd, rw, rbase[h], rbase[h] + rpark[h], 0xFFFFFFFFu, [](uint32_t) {});
+      ok_s = ok;
+    }
+    __syncthreads();
+    if (ok_s) break;
+    __syncthreads();
+  }
+  if (!ok_s) {
+    if (threadIdx.x == 0) atomicOr(err, kErrRibbon);
+    return;
+  }
+  if (threadIdx.x != 0) return;
+  seeds[sh] = (uint8_t)seed_s;
+  // Back substitution from the top: x[i] = rhs[i] + parity(row[i] bits
+  // 1..127 & x[i+1 .. i+127]) on pivot slots, 0 elsewhere; the window
+  // (wlo, whi) holds x[i+1 .. i+128].  Finished 64-bit words of the shard's
+  // bits are ORed into the global vector at the shard's bit offset.
+  uint64_t wlo = 0, whi = 0, word = 0;
+  for (int64_t i = (int64_t)m - 1; i >= 0; i--) {
+    uint64_t v = 0;
+    const uint64_t rl = bd.lo[i];
+    if (rl) {
+      const uint64_t rh = bd.hi[i];
+      const uint64_t slo = (rl >> 1) | (rh << 63), shi = rh >> 1;
+      v = (uint64_t)((bd.rhs[i] ^ __popcll(slo & wlo) ^ __popcll(shi & whi)) & 1);
+    }
+    whi = (whi << 1) | (wlo >> 63);
+    wlo = (wlo << 1) | v;
+    word |= v << (i & 63);
+    if ((i & 63) == 0) {
+      if (word) {
+        const uint64_t p = base + (uint64_t)i;
+        const uint32_t s = (uint32_t)(p & 63);
+        atomicOr((unsigned long long*)&sol_words[p >> 6], (unsigned long long)(word << s));
+        if (s && (word >> (64 - s)))
+          atomicOr((unsigned long long*)&sol_words[(p >> 6) + 1], (unsigned long long)(word >> (64 - s)));
+      }
+      word = 0;
+    }
+  }
+}
+
 shk_status launch_ribbon(Ctx& c, const uint64_t* lo, const uint64_t* hi, const uint8_t* f,
-                         const uint32_t* K, uint64_t B, uint32_t S, uint32_t eps_num,
+                         const uint32_t* K, uint64_t B, uint32_t S, uint32_t eps_num, uint32_t w,
                          uint64_t num_shards, const uint64_t* shard_off, uint32_t max_shard_slots,
-                         uint64_t* sol_words, uint8_t* seeds, uint32_t* err) {
+                         uint64_t total_slots, uint64_t n_keys, uint64_t* sol_words, uint8_t* seeds,
+                         uint32_t* err) {
   if (num_shards == 0) return SHK_OK;
+  if (w == 128) {
+    Band128 band;
+    Rows128 rows;
+    SHK_TRY(c.arena.alloc(&band.lo, total_slots));
+    SHK_TRY(c.arena.alloc(&band.hi, total_slots));
+    SHK_TRY(c.arena.alloc(&band.rhs, total_slots));
+    SHK_TRY(c.arena.alloc(&rows.lo, n_keys));
+    SHK_TRY(c.arena.alloc(&rows.hi, n_keys));
+    SHK_TRY(c.arena.alloc(&rows.start, n_keys));
+    SHK_TRY(c.arena.alloc(&rows.list, n_keys));
+    SHK_TRY(c.arena.alloc(&rows.bit, n_keys));
+    k_ribbon128<<<(unsigned)num_shards, kRibbonThreads, 0, c.stream>>>(
+        lo, hi, f, K, B, S, eps_num, shard_off, band, rows, sol_words, seeds, err);
+    c.launches++;
+    SHK_CUDA(cudaGetLastError());
+    return SHK_OK;
+  }
   const size_t limit = 227 * 1024;
   // max_shard_slots belongs to the largest shard, so it bounds its keys too
   const size_t smem_pre = ribbon_smem(max_shard_slots, max_shard_slots, true);

@@ -50,12 +50,15 @@ __global__ void k_rebase(uint64_t* o, uint64_t n, uint64_t base) {
 
 // Device bytes a build holds while it runs: keys staged on the device, three
 // 16-byte fingerprint copies (hashed, partitioned once and twice), the leaf
-// order copy, orientation bits, per-leaf and per-bucket arrays, the encoded
-// result; plus a fixed allowance.
+// order copy (lo, hi), orientation bytes, per-leaf arrays (up to ~30 bytes a
+// key at the smallest leaves), the 128-bit retrieval solver's band and rows
+// (~42 bytes a key; the 64-bit solver works in shared memory), per-bucket
+// arrays, the encoded result; plus a fixed allowance.
 uint64_t footprint(uint64_t n_keys, const shk_build_opts& o, uint64_t key_bytes) {
   const uint64_t b = o.bucket_size ? o.bucket_size : 1;
   const uint64_t buckets = n_keys / b + 1;
-  return key_bytes + n_keys * 80 + buckets * 96 + (8ull << 20);
+  const uint64_t per_key = shk::ribbon_width(o.leaf_size) == 128 ? 112 : 96;
+  return key_bytes + n_keys * per_key + buckets * 96 + (8ull << 20);
 }
 
 }  // namespace

@@ -1,6 +1,6 @@
 // shk_internal.cuh -- shared definitions of the GB300 ShockHash-RS library.
 //
-// Format constants and the arithmetic of the SHKRS001 format as used by the
+// Format constants and the arithmetic of the SHKRS002 format as used by the
 // kernels.  The definitions follow the paper (ShockHash, Sec. 4; ShockHash-RS,
 // Sec. 6) and the project's frozen readings for what the paper leaves open.
 #pragma once
@@ -25,17 +25,19 @@ constexpr uint64_t kLeafSalt = 0x13198A2E03707344ull;
 constexpr uint64_t kSplitSalt = 0xBE5466CF34E90C6Cull;
 constexpr uint64_t kRetSalt = 0xC0AC29B7C97C50DDull;
 constexpr uint64_t kRetSalt2 = 0x3F84D5B5B5470917ull;
+constexpr uint64_t kRetSalt3 = 0xA4093822299F31D0ull;
 constexpr uint64_t kStrSaltA = 0x9216D5D98979FB1Bull;
 constexpr uint64_t kStrSaltB = 0xD1310BA698DFB5ACull;
 constexpr uint64_t kRfSalt = 0x2FFD72DBD01ADFB7ull;  // rotation fitting: set split
-constexpr uint64_t kMagic = 0x31303053524B4853ull;  // "SHKRS001"
+constexpr uint64_t kMagic = 0x32303053524B4853ull;  // "SHKRS002"
 constexpr uint32_t kHeaderWords = 16;
 constexpr uint32_t kMaxLeaf = 64;
 constexpr uint32_t kMaxBucketSize = 4096;   // largest accepted b
 constexpr uint32_t kMaxBucketKeys = 8192;   // largest bucket the kernels hold
 constexpr uint64_t kSeedCap = 1ull << 40;   // seeds searched below this
 constexpr uint32_t kRibbonSeeds = 256;      // shard seeds tried
-constexpr uint32_t kDefaultEpsNum = 3277;   // eps ~ 5 %
+constexpr uint32_t kDefaultEpsNum = 3277;   // eps ~ 5 % (64-bit rows)
+constexpr uint32_t kDefaultEpsNum128 = 164;  // eps ~ 0.25 % (128-bit rows)
 constexpr uint32_t kNoCode = 0xFFFFFFFFu;
 
 // device error flags (bit set in a u32 word)
@@ -176,18 +178,35 @@ __host__ __device__ __forceinline__ void value_cells(uint32_t leaf_mode, uint64_
     leaf_cells(x, mix64(kLeafSalt + value), m, h0, h1);
 }
 
-// Retrieval row of one key in a shard of m slots with shard seed r.
-__host__ __device__ __forceinline__ void ribbon_row(uint64_t lo, uint64_t hi, uint32_t r,
-                                                    uint64_t m, uint64_t* start,
-                                                    uint64_t* coeff) {
-  const uint64_t t = mix64(hi ^ (kRetSalt + r));
-  const uint64_t u = mix64(lo ^ t);
-  *start = mulhi64(u, m - 63);
-  *coeff = mix64(u ^ kRetSalt2) | 1ull;
+// Retrieval row width w (paper Sec. 8.2: 128-bit words, 64 bits for n <= 24).
+__host__ __device__ __forceinline__ uint32_t ribbon_width(uint32_t n) { return n > 24 ? 128u : 64u; }
+
+// Defaults per width: shards of about 8,192 keys and eps = 5 % (w = 64),
+// 16,384 keys and eps = 0.25 % (w = 128).
+__host__ __device__ __forceinline__ uint32_t default_shard_buckets(uint32_t b, uint32_t w) {
+  const uint32_t s = (w == 128 ? 16384u : 8192u) / b;
+  return s ? s : 1u;
 }
 
-__host__ __device__ __forceinline__ uint64_t shard_slots(uint64_t keys, uint32_t eps_num) {
-  return keys ? keys + (keys * eps_num + 65535) / 65536 + 63 : 0;
+__host__ __device__ __forceinline__ uint32_t default_eps_num(uint32_t w) {
+  return w == 128 ? kDefaultEpsNum128 : kDefaultEpsNum;
+}
+
+// Retrieval row of one key in a shard of m slots of width w with shard seed
+// r: band start in [0, m - w] and the coefficient bits 0..63 (c0, bit 0 set)
+// and 64..127 (c1; 0 for w = 64).
+__host__ __device__ __forceinline__ void ribbon_row(uint64_t lo, uint64_t hi, uint32_t r,
+                                                    uint64_t m, uint32_t w, uint64_t* start,
+                                                    uint64_t* c0, uint64_t* c1) {
+  const uint64_t t = mix64(hi ^ (kRetSalt + r));
+  const uint64_t u = mix64(lo ^ t);
+  *start = mulhi64(u, m - (w - 1));
+  *c0 = mix64(u ^ kRetSalt2) | 1ull;
+  *c1 = w == 128 ? mix64(u ^ kRetSalt3) : 0ull;
+}
+
+__host__ __device__ __forceinline__ uint64_t shard_slots(uint64_t keys, uint32_t eps_num, uint32_t w) {
+  return keys ? keys + (keys * eps_num + 65535) / 65536 + (w - 1) : 0;
 }
 
 __host__ __device__ __forceinline__ uint32_t ef_low_bits(uint64_t U, uint64_t c) {

@@ -48,7 +48,7 @@ def test_binding_names_match_the_abi(lib):
     pkg.load_library()
     for name in _declared():
         assert callable(getattr(pkg, name)), name
-    assert pkg.shk_version() == "SHKRS001"
+    assert pkg.shk_version() == "SHKRS002"
 
 
 def test_host_side_argument_errors_without_gpu(lib):

@@ -271,17 +271,17 @@ def test_million_keys_leaf48_sampled(pkg, orc):
         codes, end = bl.rice_codes(int(O[i]), [int(k) for k in ks])
         assert codes == [int(s) for s in seeds]
         assert end == O[i + 1]
-        if i == 3:  # shard 0 = buckets 0..3
-            S = bl.h["shard_buckets"]
-            assert S == 4
-            parts = [orc.bucket_build(lo[order[K[j]:K[j + 1]]], hi[order[K[j]:K[j + 1]]], n) for j in range(S)]
-            slo = np.concatenate([p[2] for p in parts])
-            shi = np.concatenate([p[3] for p in parts])
-            sf = np.concatenate([p[4] for p in parts])
-            seed, sol = orc.ribbon_shard(slo, shi, sf, bl.h["eps_num"])
-            assert seed == bl.shard_seeds[0]
-            got = [Blob.bit(bl.ribbon, p) for p in range(sol.size)]
-            assert got == [int(v) for v in sol]
+    # retrieval shard 0 = buckets 0..7 (128-bit rows at leaf size 48)
+    S = bl.h["shard_buckets"]
+    assert S == 8 and bl.h["ribbon_width"] == 128
+    parts = [orc.bucket_build(lo[order[K[j]:K[j + 1]]], hi[order[K[j]:K[j + 1]]], n) for j in range(S)]
+    slo = np.concatenate([p[2] for p in parts])
+    shi = np.concatenate([p[3] for p in parts])
+    sf = np.concatenate([p[4] for p in parts])
+    seed, sol = orc.ribbon_shard(slo, shi, sf, bl.h["eps_num"], 128)
+    assert seed == bl.shard_seeds[0]
+    got = [Blob.bit(bl.ribbon, p) for p in range(sol.size)]
+    assert got == [int(v) for v in sol]
     samp = np.arange(0, N, 37)
     r_or = orc.query(blob, lo[samp], hi[samp])
     assert np.array_equal(r_or, ranks.cpu().numpy().view(np.uint64)[samp])

@@ -74,10 +74,10 @@ MUTANTS = [
      lambda o: build_pins.test_format_sections_decode(o)),
     ("retrieval: free columns set to one",
      "      sol[ii] = 0;\n      continue;", "      sol[ii] = 1;\n      continue;",
-     lambda o: pins.test_ribbon_canonical_solution(o, 60, 3277)),
+     lambda o: pins.test_ribbon_canonical_solution(o, 60, 3277, 128)),
     ("retrieval: band start range one slot short",
-     "*start = (uint64_t)(((u128)u * (m - 63)) >> 64);", "*start = (uint64_t)(((u128)u * (m - 64)) >> 64);",
-     lambda o: pins.test_ribbon_row_start_uniform_and_coefficients_balanced(o)),
+     "*start = (uint64_t)(((u128)u * (m - (w - 1))) >> 64);", "*start = (uint64_t)(((u128)u * (m - w)) >> 64);",
+     lambda o: pins.test_ribbon_row_start_uniform_and_coefficients_balanced(o, 128)),
     ("retrieval: orientation bits stored inverted",
      "    uint8_t b = f[i];", "    uint8_t b = f[i] ^ 1u;",
      lambda o: build_pins.test_build_is_bijection(o, 3000, 8, 100)),
@@ -112,11 +112,18 @@ MUTANTS = [
      "hi[i] = orc_siphash24(STR_SALT_B, STR_SALT_A, p, len);", "hi[i] = orc_siphash24(STR_SALT_A, STR_SALT_B, p, len);",
      lambda o: pins.test_string_fingerprint_is_keyed_siphash_and_sensitive(o)),
     ("retrieval row: coefficient bit 0 not forced",
-     "*coeff = orc_mix64(u ^ RET_SALT2) | 1ull;", "*coeff = orc_mix64(u ^ RET_SALT2);",
-     lambda o: pins.test_ribbon_row_start_uniform_and_coefficients_balanced(o)),
+     "uint64_t c0 = orc_mix64(u ^ RET_SALT2) | 1ull;", "uint64_t c0 = orc_mix64(u ^ RET_SALT2);",
+     lambda o: pins.test_ribbon_row_start_uniform_and_coefficients_balanced(o, 64)),
     ("retrieval row: band start over half the range",
-     "*start = (uint64_t)(((u128)u * (m - 63)) >> 64);", "*start = (uint64_t)(((u128)u * (m - 63)) >> 65);",
-     lambda o: pins.test_ribbon_row_start_uniform_and_coefficients_balanced(o)),
+     "*start = (uint64_t)(((u128)u * (m - (w - 1))) >> 64);", "*start = (uint64_t)(((u128)u * (m - (w - 1))) >> 65);",
+     lambda o: pins.test_ribbon_row_start_uniform_and_coefficients_balanced(o, 64)),
+    ("retrieval: 128-bit rows keep only their low word",
+     "uint64_t c1 = w == 128 ? orc_mix64(u ^ RET_SALT3) : 0;", "uint64_t c1 = 0;",
+     lambda o: pins.test_ribbon_row_start_uniform_and_coefficients_balanced(o, 128)),
+    ("retrieval: 128-bit band back substitution stops at bit 63",
+     "    for (uint32_t j = 1; j < w; j++)\n      if ((rows[ii] >> j) & 1) b ^= sol[ii + j];",
+     "    for (uint32_t j = 1; j < 64; j++)\n      if ((rows[ii] >> j) & 1) b ^= sol[ii + j];",
+     lambda o: pins.test_ribbon_canonical_solution(o, 300, 3277, 128)),
     ("leaf hash: second cell from bits overlapping the first",
      "uint32_t t = (uint32_t)(((uint64_t)(uint32_t)w * (m - 1)) >> 32);",
      "uint32_t t = (uint32_t)(((uint64_t)(uint32_t)(w >> 8) * (m - 1)) >> 32);",

@@ -389,11 +389,11 @@ def test_rice_parameters(orc):
 # --------------------------------------------------------------------------
 # retrieval: canonical solution vs an independent dense GF(2) elimination
 # --------------------------------------------------------------------------
-def _rows_for(orc, lo, hi, seed, m):
+def _rows_for(orc, lo, hi, seed, m, w=64):
     """Each key's equation as a band: coeff << start (the oracle's rows; their
     hash is pinned statistically below)."""
-    start, coeff = orc.ribbon_rows(lo, hi, seed, m)
-    return [int(c) << int(st) for st, c in zip(start, coeff)]
+    start, coeff = orc.ribbon_rows(lo, hi, seed, m, w)
+    return [c << int(st) for st, c in zip(start, coeff)]
 
 
 def _gf2_canonical(rows, rhs, m):
@@ -426,18 +426,23 @@ def _gf2_canonical(rows, rhs, m):
     return sol
 
 
-@pytest.mark.parametrize("keys,eps", [(1, 3277), (5, 3277), (40, 0), (60, 3277), (300, 3277), (500, 655)])
-def test_ribbon_canonical_solution(orc, keys, eps):
+@pytest.mark.parametrize("w", [64, 128])
+@pytest.mark.parametrize("keys,eps", [(1, 3277), (5, 3277), (40, 0), (60, 3277), (300, 3277), (500, 655),
+                                      (700, 164)])
+def test_ribbon_canonical_solution(orc, keys, eps, w):
+    """Retrieval (Sec. 2; 64- and 128-bit rows, Sec. 8.2): the stored solution
+    is the one an independent dense GF(2) elimination gives (zero on every
+    non-pivot column), and every smaller shard seed is inconsistent."""
     for t in range(4):
         lo = inp.splitmix64_stream(123 + t, keys)
         hi = inp.splitmix64_stream(456 + t, keys)
         f = (inp.splitmix64_stream(789 + t, keys) & np.uint64(1)).astype(np.uint8)
-        seed, sol = orc.ribbon_shard(lo, hi, f, eps)
-        m = orc.shard_slots(keys, eps)
-        assert m == keys + math.ceil(keys * eps / 65536) + 63
+        seed, sol = orc.ribbon_shard(lo, hi, f, eps, w)
+        m = orc.shard_slots(keys, eps, w)
+        assert m == keys + math.ceil(keys * eps / 65536) + w - 1
         for s2 in range(seed):  # every smaller shard seed gives an inconsistent system
-            assert _gf2_canonical(_rows_for(orc, lo, hi, s2, m), [int(v) for v in f], m) is None
-        want = _gf2_canonical(_rows_for(orc, lo, hi, seed, m), [int(v) for v in f], m)
+            assert _gf2_canonical(_rows_for(orc, lo, hi, s2, m, w), [int(v) for v in f], m) is None
+        want = _gf2_canonical(_rows_for(orc, lo, hi, seed, m, w), [int(v) for v in f], m)
         assert want is not None
         assert [int(v) for v in sol] == want
 
@@ -447,40 +452,46 @@ def test_ribbon_empty_shard(orc):
     assert seed == 0 and sol.size == 0
 
 
-def test_ribbon_row_start_uniform_and_coefficients_balanced(orc):
+@pytest.mark.parametrize("w", [64, 128])
+def test_ribbon_row_start_uniform_and_coefficients_balanced(orc, w):
     """Retrieval rows (Sec. 2 Retrieval: each key's equation is a random band
-    of the solution): the band start is uniform over the m - 63 positions
-    (chi-square), coefficient bits 1..63 are fair coins and bit 0 is set,
+    of the solution): the band start is uniform over the m - w + 1 positions
+    (chi-square), coefficient bits 1..w-1 are fair coins and bit 0 is set,
     and a different shard seed gives unrelated rows."""
-    n, m = 200000, 1063
+    n, m = 200000, 1000 + w - 1
     lo = inp.splitmix64_stream(601, n)
     hi = inp.splitmix64_stream(602, n)
-    start, coeff = orc.ribbon_rows(lo, hi, 0, m)
-    # every band start 0 .. m - 64 occurs (the last band ends at slot m - 1)
-    assert int(start.min()) == 0 and int(start.max()) == m - 64
-    cnt = np.bincount(start.astype(np.int64), minlength=m - 63)
-    exp = n / (m - 63)
+    start, coeff = orc.ribbon_rows(lo, hi, 0, m, w)
+    # every band start 0 .. m - w occurs (the last band ends at slot m - 1)
+    assert int(start.min()) == 0 and int(start.max()) == m - w
+    cnt = np.bincount(start.astype(np.int64), minlength=m - w + 1)
+    exp = n / (m - w + 1)
     chi2 = float(((cnt - exp) ** 2 / exp).sum())
-    dof = m - 64
+    dof = m - w
     assert abs(chi2 - dof) < 5 * math.sqrt(2 * dof)
-    bits = ((coeff[:, None] >> np.arange(64, dtype=np.uint64)) & np.uint64(1)).astype(np.float64)
+    words = np.array([[c & (2**64 - 1), c >> 64] for c in coeff], dtype=np.uint64)
+    bits = np.concatenate([((words[:, j:j + 1] >> np.arange(64, dtype=np.uint64)) & np.uint64(1))
+                           for j in range(w // 64)], axis=1).astype(np.float64)
     freq = bits.mean(axis=0)
     assert freq[0] == 1.0
     assert np.all(np.abs(freq[1:] - 0.5) < 4.5 * math.sqrt(0.25 / n))
-    # start and coefficient are not tied: the low coefficient bits do not move the start
-    for b in (1, 2, 7, 40):
+    if w == 64:
+        assert np.all(words[:, 1] == 0)
+    # start and coefficient are not tied: coefficient bits do not move the start
+    for b in (1, 2, 7, 40, w - 1):
         sel = bits[:, b] == 1
-        assert abs(start[sel].astype(np.float64).mean() - start[~sel].astype(np.float64).mean()) < 5 * (m - 63) / math.sqrt(12 * n / 4)
-    s1, c1 = orc.ribbon_rows(lo, hi, 1, m)
-    assert (s1 == start).mean() < 3 / (m - 63)
-    assert not np.any(c1 == coeff)
+        assert abs(start[sel].astype(np.float64).mean() - start[~sel].astype(np.float64).mean()) < 5 * (m - w + 1) / math.sqrt(12 * n / 4)
+    s1, c1 = orc.ribbon_rows(lo, hi, 1, m, w)
+    assert (s1 == start).mean() < 3 / (m - w + 1)
+    assert not any(a == b for a, b in zip(c1, coeff))
 
 
 def _band_consistent(start, coeff, f):
     """Gaussian elimination over GF(2) on rows coeff << start (Python ints):
     True iff the system has a solution."""
     piv = {}
-    for s0, c, b in zip(start.tolist(), coeff.tolist(), f.tolist()):
+    coeff = coeff.tolist() if hasattr(coeff, "tolist") else coeff
+    for s0, c, b in zip(start.tolist(), coeff, f.tolist()):
         r = c << s0
         while r:
             p = (r & -r).bit_length() - 1
@@ -496,25 +507,29 @@ def _band_consistent(start, coeff, f):
     return True
 
 
-@pytest.mark.parametrize("eps", [983, 3277])
-def test_ribbon_shard_success_rate_matches_random_rows(orc, eps):
+@pytest.mark.parametrize("k,eps,w,T", [(8000, 983, 64, 300), (8000, 3277, 64, 300), (16000, 164, 128, 100)])
+def test_ribbon_shard_success_rate_matches_random_rows(orc, k, eps, w, T):
     """A shard seed succeeds as often as a ribbon system of numpy-random rows
-    of the same size (8,000 keys, eps = 1.5 % and 5 %): the row hash behaves
-    like the random bands the retrieval structure assumes."""
-    k, T = 8000, 300
-    m = orc.shard_slots(k, eps)
+    of the same size (8,000 keys at eps = 1.5 % and 5 % with 64-bit rows;
+    16,000 keys at eps = 0.25 % with 128-bit rows, the defaults): the row
+    hash behaves like the random bands the retrieval structure assumes."""
+    m = orc.shard_slots(k, eps, w)
     ok = 0
     for i in range(T):
         lo = inp.splitmix64_stream(10_000 + i, k)
         hi = inp.splitmix64_stream(20_000 + i, k)
         f = (inp.splitmix64_stream(30_000 + i, k) & np.uint64(1)).astype(np.uint8)
-        seed, _ = orc.ribbon_shard(lo, hi, f, eps)
+        seed, _ = orc.ribbon_shard(lo, hi, f, eps, w)
         ok += seed == 0
     rng = np.random.default_rng(eps)
     sim = 0
     for _ in range(T):
-        st = rng.integers(0, m - 63, k)
-        co = (rng.integers(0, 2**63, k, dtype=np.int64).astype(np.uint64) << np.uint64(1)) | np.uint64(1)
+        st = rng.integers(0, m - w + 1, k)
+        words = [(rng.integers(0, 2**63, k, dtype=np.int64).astype(np.uint64) << np.uint64(1)) | np.uint64(1)]
+        if w == 128:
+            words.append(rng.integers(0, 2**63, k, dtype=np.int64).astype(np.uint64) << np.uint64(1)
+                         | rng.integers(0, 2, k).astype(np.uint64))
+        co = [int(a) | (int(b) << 64) for a, b in zip(words[0], words[1])] if w == 128 else words[0]
         sim += _band_consistent(st, co, rng.integers(0, 2, k))
     p1, p2 = ok / T, sim / T
     p = (p1 + p2) / 2
