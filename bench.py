@@ -455,6 +455,8 @@ def run_ours(args):
         "input_generation_s": gen_s,
         "wall_s_timed": wall,
         "u64_1M_leaf48": u64rec,
+        "served_builds": {} if args.no_subrecords else serve_run(pkg, args.serve_requests, args.serve_max_keys,
+                                                                  True, rank),
     }
     if clocks:
         line["clocks"] = clocks
@@ -562,28 +564,26 @@ def run_leafbatch(args):
     return 0
 
 
-def run_serve(args):
+def serve_run(pkg, requests: int, max_keys: float, rf: bool, rank: int = 0, check_alone: bool = True,
+              clk=None) -> dict:
     """Served builds: a Poisson stream of MPHF build requests (uniform u64
-    keys, sizes log-uniform in [1e3, max_keys], leaf size 48 or 58 by coin,
-    bucket 2000, stream seed 5, request i from sub-seed 5 + 7919 i) into one
-    server with 4 builds in flight; plain or rotation-fitting leaves.  The
-    arrival rate is set for ~80 % offered load from a calibration build of
-    each leaf size.  Reports p50/p99 build latency (submit to finish) and
-    aggregate keys/s."""
+    keys generated on the device, sizes log-uniform in [1e3, max_keys], leaf
+    size 48 or 58 by coin, bucket 2000, stream seed 5, request i from sub-seed
+    5 + 7919 i) submitted as device tensors into one server with 4 builds in
+    flight; plain or rotation-fitting leaves.  The arrival rate is set for
+    ~80 % offered load from a calibration build of each leaf size.  Reports
+    p50/p99 build latency (submit to finish), aggregate keys/s, how the
+    requests' leaf-search kernels overlapped on the device (device-time
+    intervals), and whether every result equals the same build alone."""
     import torch
 
-    import paper_2308_09561_gb300 as pkg
     import shk_inputs
 
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    pkg.load_library()
-    R = args.requests
+    R = requests
     u = shk_inputs.uniform01(5 + 1000 * rank, 3 * R)
-    sizes = np.floor(10 ** (3 + np.log10(args.max_keys / 1e3) * u[0::3])).astype(np.int64)
-    mode = pkg.SHK_LEAF_ROTATION if args.serve_rf else pkg.SHK_LEAF_PLAIN
+    sizes = np.floor(10 ** (3 + np.log10(max_keys / 1e3) * u[0::3])).astype(np.int64)
+    mode = pkg.SHK_LEAF_ROTATION if rf else pkg.SHK_LEAF_PLAIN
     leafs = np.where(u[1::3] < 0.5, 48, 58)
-    # request keys are generated on the device (the same keys as distinct_u64)
     reqs = [(shk_inputs.splitmix64_stream_torch(5 + 7919 * i + 1000003 * rank, int(sz), device="cuda"), int(n))
             for i, (sz, n) in enumerate(zip(sizes, leafs))]
     torch.cuda.synchronize()
@@ -599,43 +599,71 @@ def run_serve(args):
     rate = 0.8 / service
     gaps = -np.log(1.0 - shk_inputs.uniform01(55 + 1000 * rank, R)) / rate
     srv = pkg.shk_server_create(0, 4)
-    pending, infos = {}, []
+    pending, infos, blobs, spans = {}, {}, {}, []
+
+    def collect(rid, m, info):
+        i = pending.pop(rid)
+        infos[i] = info
+        if m is not None:
+            st = m.stats()
+            spans.append((st["leaf_t0_ns"], st["leaf_t1_ns"]))
+            if check_alone:
+                blobs[i] = m.serialize()
+            m.close()
+
     t0 = time.perf_counter()
     arrivals = t0 + np.cumsum(gaps)
-    with ClockSampler(local) as clk:
-        for i, (keys, n) in enumerate(reqs):
-            while time.perf_counter() < arrivals[i]:
-                for rid in list(pending):
-                    m, info = pkg.shk_server_poll(srv, rid)
-                    if info["done"]:
-                        infos.append(info)
-                        pending.pop(rid)
-                        if m is not None:
-                            m.close()
-                time.sleep(0.0005)
-            pending[pkg.shk_server_submit(srv, keys, n, BUCKET, leaf_mode=mode)] = i
-        for rid in list(pending):
-            m, info = pkg.shk_server_wait(srv, rid)
-            infos.append(info)
-            if m is not None:
-                m.close()
+    for i, (keys, n) in enumerate(reqs):
+        while time.perf_counter() < arrivals[i]:
+            for rid in list(pending):
+                m, info = pkg.shk_server_poll(srv, rid)
+                if info["done"]:
+                    collect(rid, m, info)
+            time.sleep(0.0005)
+        pending[pkg.shk_server_submit(srv, keys, n, BUCKET, leaf_mode=mode)] = i
+    for rid in list(pending):
+        m, info = pkg.shk_server_wait(srv, rid)
+        collect(rid, m, info)
     st = pkg.shk_server_get_stats(srv)
     pkg.shk_server_destroy(srv)
-    lat = np.array([(i["finish_ns"] - i["submit_ns"]) / 1e6 for i in infos])
-    ok = all(i["status"] == 0 for i in infos)
-    span = (max(i["finish_ns"] for i in infos) - min(i["submit_ns"] for i in infos)) / 1e9
+    lat = np.array([(infos[i]["finish_ns"] - infos[i]["submit_ns"]) / 1e6 for i in range(R)])
+    ok = all(infos[i]["status"] == 0 for i in range(R))
+    span = (max(i["finish_ns"] for i in infos.values()) - min(i["submit_ns"] for i in infos.values())) / 1e9
     total = int(sum(k.numel() for k, _ in reqs))
-    line = {"metric": "served MPHF builds: aggregate keys/s, p50/p99 latency", "value": total / span,
+    spans = sorted(x for x in spans if x[1] > x[0])
+    busy = sum(b - a for a, b in spans)
+    overlapping = sum(1 for j, (a, b) in enumerate(spans) if any(a < d and c < b for c, d in spans[:j]))
+    rec = {"workload": "served_builds_poisson", "requests": R, "sizes": f"log-uniform [1e3, {max_keys:.0e}]",
+           "leaf_sizes": [48, 58], "leaf_mode": "rf" if rf else "plain", "bucket_size": BUCKET,
+           "offered_load": 0.8, "workers": 4, "keys_submitted_as": "device tensors (kept on the device)",
+           "keys_per_s": total / span, "p50_ms": float(np.percentile(lat, 50)),
+           "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "all_ok": ok,
+           "total_keys": total, "makespan_s": span, "arrival_rate_per_s": rate,
+           "calibration_s_per_key": per_key, "peak_reserved_bytes": st["peak_in_use_bytes"],
+           "leaf_kernels": {"requests_overlapping_an_earlier_one": overlapping,
+                            "busy_s_summed": busy / 1e9,
+                            "first_start_to_last_end_s": (spans[-1][1] - spans[0][0]) / 1e9 if spans else 0.0}}
+    if check_alone:
+        same = all(pkg.shk_build(k, n, BUCKET, leaf_mode=mode).serialize() == blobs[i]
+                   for i, (k, n) in enumerate(reqs))
+        rec["all_equal_to_alone"] = bool(same)
+    return rec
+
+
+def run_serve(args):
+    """The served-builds workload alone (serve_run) as one JSON line."""
+    import torch
+
+    import paper_2308_09561_gb300 as pkg
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pkg.load_library()
+    with ClockSampler(local) as clk:
+        rec = serve_run(pkg, args.requests, args.max_keys, args.serve_rf, rank)
+    line = {"metric": "served MPHF builds: aggregate keys/s, p50/p99 latency", "value": rec["keys_per_s"],
             "unit": "keys/s", "n_gpus": ws, "steps": 1, "warmup": 2, "higher_is_better": True,
-            "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "served_builds_poisson", "requests": R,
-                       "sizes": f"log-uniform [1e3, {args.max_keys:.0e}]", "leaf_sizes": [48, 58],
-                       "leaf_mode": "rf" if args.serve_rf else "plain", "bucket_size": BUCKET,
-                       "offered_load": 0.8, "workers": 4},
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "all_ok": ok, "total_keys": total, "makespan_s": span,
-            "arrival_rate_per_s": rate, "calibration_s_per_key": per_key,
-            "peak_reserved_bytes": st["peak_in_use_bytes"]}
+            "dtype": "u64", "data": "synthetic", "config": {"workload": rec["workload"]}, **rec}
     clocks = clk.summary()
     if clocks:
         line["clocks"] = clocks
@@ -691,6 +719,10 @@ def main():
     ap.add_argument("--max-keys", type=float, default=3e5,
                     help="serve: largest request (sizes log-uniform from 1e3; 1e7 in the full stream)")
     ap.add_argument("--serve-rf", action="store_true", help="serve: rotation-fitting leaves")
+    ap.add_argument("--serve-requests", type=int, default=60,
+                    help="headline run: requests of its served-builds sub-record (rotation fitting)")
+    ap.add_argument("--serve-max-keys", type=float, default=1e6,
+                    help="headline run: largest request of its served-builds sub-record")
     ap.add_argument("--eps-num", type=int, default=STR_EPS,
                     help="headline: retrieval overhead eps = eps_num / 65536 (0: the library default, "
                          "164 (0.25 %%) for the 128-bit rows of leaf size 64)")
