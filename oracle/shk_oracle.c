@@ -930,13 +930,13 @@ static void put_words(uint8_t* out, uint64_t* pos_words, const uint64_t* w, uint
 }
 
 /* Retrieval defaults per ribbon width: shards of about 8,192 keys and
- * eps = 5 % (w = 64), 16,384 keys and eps = 0.25 % (w = 128). */
+ * eps = 5 % (w = 64), 12,288 keys and eps = 0.1 % (w = 128). */
 uint32_t orc_default_shard_buckets(uint32_t b, uint32_t w) {
-  uint32_t s = (w == 128 ? 16384u : 8192u) / b;
+  uint32_t s = (w == 128 ? 12288u : 8192u) / b;
   return s ? s : 1u;
 }
 
-uint32_t orc_default_eps_num(uint32_t w) { return w == 128 ? 164u : 3277u; }
+uint32_t orc_default_eps_num(uint32_t w) { return w == 128 ? 66u : 3277u; }
 
 int orc_build(int kind, const void* data, const uint64_t* offs, uint64_t N, uint32_t n,
               uint32_t b, uint32_t shard_buckets, uint32_t eps_num, int nthreads, int leaf_mode,

@@ -22,6 +22,12 @@ namespace shk {
 
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
 constexpr int kRfSeeds = 8;  // seeds per lane (= the partial-hash period)
+// Missed cells of each 32-cell half (m = 64) intersected without branches
+// before the surviving rotations are checked one by one (even; the result
+// does not depend on it).
+#ifndef SHK_RF_HALF
+#define SHK_RF_HALF 12
+#endif
 
 struct RfScratch {
   uint64_t x[kMaxLeaf];  // leaf inputs (multiplier bit set), set A first
@@ -77,8 +83,9 @@ __device__ __forceinline__ void rf_rotations8(uint64_t ma, const uint64_t* mb, u
   uint64_t z;
   if (M64) {
     // the 64 cells as two 32-bit halves: a rotation by c < 32 (cells of the
-    // low half) or by 32 + c (high half) is a pair of funnel shifts
-    constexpr int kHalf = 12;
+    // low half) or by 32 + c (high half) is a pair of funnel shifts; up to
+    // kHalf missed cells of each half are intersected without branches
+    constexpr int kHalf = SHK_RF_HALF;
     uint32_t zl = ~(uint32_t)ma, zh = ~(uint32_t)(ma >> 32);
     uint32_t rl[kRfSeeds], rh[kRfSeeds], bl[kRfSeeds], bh[kRfSeeds];
 #pragma unroll

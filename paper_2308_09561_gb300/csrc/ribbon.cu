@@ -345,11 +345,14 @@ __global__ void __launch_bounds__(kRibbonThreads)
 }
 
 // ---------------------------------------------------------------------------
-// 128-bit rows (leaf size n > 24).  At the default shard size (about 16,400
-// keys) a shard's band (16 bytes of row and 1 byte of right-hand side per
-// slot) does not fit shared memory, so the band and the per-key rows live in
-// global scratch indexed by global slot / key; a shard's working set (~0.7 MB)
-// stays in L1/L2.  The elimination is the region-parallel one of k_ribbon:
+// 128-bit rows (leaf size n > 24).  A shard's band (16 bytes of row and 1 byte
+// of right-hand side per slot, ~210 KB at the default ~12,000 keys) lives in
+// shared memory (SMEM) -- or, for a shard too large for it, in global scratch
+// indexed by global slot -- and the per-key rows (read once per key and
+// seed) in global scratch indexed by global key.  Every elimination step reads
+// the band, so it must be in shared memory to be fast: in global memory (L2
+// round trips) the solve was ~60x slower.  The elimination is the
+// region-parallel one of k_ribbon:
 // lane 0 of warp g eliminates the rows that start in region g, rows that step
 // past their region are parked and continue in rounds through the following
 // regions, and thread 0 finishes any rows still parked.
@@ -425,11 +428,16 @@ __device__ __forceinline__ int eliminate_list128(const Band128& bd, const Rows12
   return 1;
 }
 
+// Shared memory of one shard's band: lo[m] u64 | hi[m] u64 | rhs[m] u8.
+__host__ __device__ inline size_t ribbon128_smem(uint64_t m) { return (size_t)m * 17 + 16; }
+
+template <bool SMEM>
 __global__ void __launch_bounds__(kRibbonThreads)
     k_ribbon128(const uint64_t* __restrict__ lo, const uint64_t* __restrict__ hi,
                 const uint8_t* __restrict__ f, const uint32_t* __restrict__ K, uint64_t B, uint32_t S,
                 uint32_t eps_num, const uint64_t* __restrict__ shard_off, Band128 band, Rows128 rows,
                 uint64_t* sol_words, uint8_t* seeds, uint32_t* err) {
+  extern __shared__ uint64_t band_smem[];
   const uint64_t sh = blockIdx.x;
   const uint64_t b0 = sh * S, b1 = b0 + S < B ? b0 + S : B;
   const uint32_t k0 = K[b0], keys = K[b1] - K[b0];
@@ -439,7 +447,8 @@ __global__ void __launch_bounds__(kRibbonThreads)
     return;
   }
   const uint64_t base = shard_off[sh];
-  const Band128 bd{band.lo + base, band.hi + base, band.rhs + base};
+  const Band128 bd = SMEM ? Band128{band_smem, band_smem + m, (uint8_t*)(band_smem + 2 * m)}
+                          : Band128{band.lo + base, band.hi + base, band.rhs + base};
   const Rows128 rw{rows.lo + k0, rows.hi + k0, rows.start + k0, rows.list + k0, rows.bit + k0};
   __shared__ int ok_s;
   __shared__ uint32_t seed_s;
@@ -560,18 +569,25 @@ shk_status launch_ribbon(Ctx& c, const uint64_t* lo, const uint64_t* hi, const u
                          uint32_t* err) {
   if (num_shards == 0) return SHK_OK;
   if (w == 128) {
-    Band128 band;
+    Band128 band{nullptr, nullptr, nullptr};
     Rows128 rows;
-    SHK_TRY(c.arena.alloc(&band.lo, total_slots));
-    SHK_TRY(c.arena.alloc(&band.hi, total_slots));
-    SHK_TRY(c.arena.alloc(&band.rhs, total_slots));
     SHK_TRY(c.arena.alloc(&rows.lo, n_keys));
     SHK_TRY(c.arena.alloc(&rows.hi, n_keys));
     SHK_TRY(c.arena.alloc(&rows.start, n_keys));
     SHK_TRY(c.arena.alloc(&rows.list, n_keys));
     SHK_TRY(c.arena.alloc(&rows.bit, n_keys));
-    k_ribbon128<<<(unsigned)num_shards, kRibbonThreads, 0, c.stream>>>(
-        lo, hi, f, K, B, S, eps_num, shard_off, band, rows, sol_words, seeds, err);
+    const size_t smem = ribbon128_smem(max_shard_slots);
+    if (smem <= 227 * 1024) {
+      SHK_TRY(raise_smem_limit((const void*)k_ribbon128<true>, smem));
+      k_ribbon128<true><<<(unsigned)num_shards, kRibbonThreads, smem, c.stream>>>(
+          lo, hi, f, K, B, S, eps_num, shard_off, band, rows, sol_words, seeds, err);
+    } else {  // a shard too large for shared memory: the band in global scratch
+      SHK_TRY(c.arena.alloc(&band.lo, total_slots));
+      SHK_TRY(c.arena.alloc(&band.hi, total_slots));
+      SHK_TRY(c.arena.alloc(&band.rhs, total_slots));
+      k_ribbon128<false><<<(unsigned)num_shards, kRibbonThreads, 0, c.stream>>>(
+          lo, hi, f, K, B, S, eps_num, shard_off, band, rows, sol_words, seeds, err);
+    }
     c.launches++;
     SHK_CUDA(cudaGetLastError());
     return SHK_OK;

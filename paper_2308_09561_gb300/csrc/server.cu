@@ -51,8 +51,8 @@ __global__ void k_rebase(uint64_t* o, uint64_t n, uint64_t base) {
 // Device bytes a build holds while it runs: keys staged on the device, three
 // 16-byte fingerprint copies (hashed, partitioned once and twice), the leaf
 // order copy (lo, hi), orientation bytes, per-leaf arrays (up to ~30 bytes a
-// key at the smallest leaves), the 128-bit retrieval solver's band and rows
-// (~42 bytes a key; the 64-bit solver works in shared memory), per-bucket
+// key at the smallest leaves), the 128-bit retrieval solver's per-key rows
+// (25 bytes a key, up to 42 with an oversized shard's band), per-bucket
 // arrays, the encoded result; plus a fixed allowance.
 uint64_t footprint(uint64_t n_keys, const shk_build_opts& o, uint64_t key_bytes) {
   const uint64_t b = o.bucket_size ? o.bucket_size : 1;

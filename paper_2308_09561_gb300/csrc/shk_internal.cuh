@@ -37,7 +37,7 @@ constexpr uint32_t kMaxBucketKeys = 8192;   // largest bucket the kernels hold
 constexpr uint64_t kSeedCap = 1ull << 40;   // seeds searched below this
 constexpr uint32_t kRibbonSeeds = 256;      // shard seeds tried
 constexpr uint32_t kDefaultEpsNum = 3277;   // eps ~ 5 % (64-bit rows)
-constexpr uint32_t kDefaultEpsNum128 = 164;  // eps ~ 0.25 % (128-bit rows)
+constexpr uint32_t kDefaultEpsNum128 = 66;   // eps ~ 0.1 % (128-bit rows)
 constexpr uint32_t kNoCode = 0xFFFFFFFFu;
 
 // device error flags (bit set in a u32 word)
@@ -182,9 +182,10 @@ __host__ __device__ __forceinline__ void value_cells(uint32_t leaf_mode, uint64_
 __host__ __device__ __forceinline__ uint32_t ribbon_width(uint32_t n) { return n > 24 ? 128u : 64u; }
 
 // Defaults per width: shards of about 8,192 keys and eps = 5 % (w = 64),
-// 16,384 keys and eps = 0.25 % (w = 128).
+// 12,288 keys and eps = 0.1 % (w = 128; the largest shards whose band fits a
+// CTA's shared memory).
 __host__ __device__ __forceinline__ uint32_t default_shard_buckets(uint32_t b, uint32_t w) {
-  const uint32_t s = (w == 128 ? 16384u : 8192u) / b;
+  const uint32_t s = (w == 128 ? 12288u : 8192u) / b;
   return s ? s : 1u;
 }
 

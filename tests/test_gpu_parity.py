@@ -271,9 +271,9 @@ def test_million_keys_leaf48_sampled(pkg, orc):
         codes, end = bl.rice_codes(int(O[i]), [int(k) for k in ks])
         assert codes == [int(s) for s in seeds]
         assert end == O[i + 1]
-    # retrieval shard 0 = buckets 0..7 (128-bit rows at leaf size 48)
+    # retrieval shard 0 = buckets 0..5 (128-bit rows at leaf size 48)
     S = bl.h["shard_buckets"]
-    assert S == 8 and bl.h["ribbon_width"] == 128
+    assert S == 6 and bl.h["ribbon_width"] == 128
     parts = [orc.bucket_build(lo[order[K[j]:K[j + 1]]], hi[order[K[j]:K[j + 1]]], n) for j in range(S)]
     slo = np.concatenate([p[2] for p in parts])
     shi = np.concatenate([p[3] for p in parts])

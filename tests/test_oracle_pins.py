@@ -507,11 +507,11 @@ def _band_consistent(start, coeff, f):
     return True
 
 
-@pytest.mark.parametrize("k,eps,w,T", [(8000, 983, 64, 300), (8000, 3277, 64, 300), (16000, 164, 128, 100)])
+@pytest.mark.parametrize("k,eps,w,T", [(8000, 983, 64, 300), (8000, 3277, 64, 300), (12000, 66, 128, 100)])
 def test_ribbon_shard_success_rate_matches_random_rows(orc, k, eps, w, T):
     """A shard seed succeeds as often as a ribbon system of numpy-random rows
     of the same size (8,000 keys at eps = 1.5 % and 5 % with 64-bit rows;
-    16,000 keys at eps = 0.25 % with 128-bit rows, the defaults): the row
+    12,000 keys at eps = 0.1 % with 128-bit rows, the default): the row
     hash behaves like the random bands the retrieval structure assumes."""
     m = orc.shard_slots(k, eps, w)
     ok = 0
