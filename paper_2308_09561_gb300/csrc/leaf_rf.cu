@@ -26,7 +26,7 @@ constexpr int kRfSeeds = 8;  // seeds per lane (= the partial-hash period)
 // before the surviving rotations are checked one by one (even; the result
 // does not depend on it).
 #ifndef SHK_RF_HALF
-#define SHK_RF_HALF 12
+#define SHK_RF_HALF 10
 #endif
 
 struct RfScratch {

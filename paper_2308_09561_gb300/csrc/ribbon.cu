@@ -366,8 +366,9 @@ struct Rows128 {  // per key, reduced state while it is parked
   uint64_t* lo;
   uint64_t* hi;
   uint32_t* start;
-  uint32_t* list;  // keys by region of their start
+  uint32_t* list;  // keys in ascending order of their start
   uint8_t* bit;
+  uint32_t* cnt;   // per start slot (indexed by global slot): counts, then offsets
 };
 
 __device__ __forceinline__ int eliminate128(const Band128& bd, uint32_t* st, uint64_t* clo,
@@ -449,44 +450,79 @@ __global__ void __launch_bounds__(kRibbonThreads)
   const uint64_t base = shard_off[sh];
   const Band128 bd = SMEM ? Band128{band_smem, band_smem + m, (uint8_t*)(band_smem + 2 * m)}
                           : Band128{band.lo + base, band.hi + base, band.rhs + base};
-  const Rows128 rw{rows.lo + k0, rows.hi + k0, rows.start + k0, rows.list + k0, rows.bit + k0};
+  const Rows128 rw{rows.lo + k0, rows.hi + k0, rows.start + k0, rows.list + k0, rows.bit + k0,
+                   rows.cnt + base};
   __shared__ int ok_s;
   __shared__ uint32_t seed_s;
-  __shared__ uint32_t rbase[kRegions + 1], rfill[kRegions], rpark[kRegions];
+  __shared__ uint32_t rbase[kRegions + 1], rpark[kRegions];
+  __shared__ uint32_t part[kRibbonThreads], wtot[kRegions];
   const uint32_t w = (uint32_t)((m + kRegions - 1) / kRegions);  // region width in slots
+  const uint32_t ns = (uint32_t)(m - 127);                        // possible start slots
+  const uint32_t per = (ns + kRibbonThreads - 1) / kRibbonThreads;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (uint32_t r = 0; r < kRibbonSeeds; r++) {
-    for (uint64_t i = threadIdx.x; i < m; i += kRibbonThreads) bd.lo[i] = 0;
-    if (threadIdx.x < kRegions) rfill[threadIdx.x] = 0;
-    if (threadIdx.x == 0) {
+    for (uint64_t i = tid; i < m; i += kRibbonThreads) bd.lo[i] = 0;
+    for (uint32_t s = tid; s < ns; s += kRibbonThreads) rw.cnt[s] = 0;
+    if (tid == 0) {
       ok_s = 1;
       seed_s = r;
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < keys; i += kRibbonThreads) {
+    for (uint32_t i = tid; i < keys; i += kRibbonThreads) {
       uint64_t st, c0, c1;
       ribbon_row(lo[k0 + i], hi[k0 + i], r, m, 128, &st, &c0, &c1);
       rw.lo[i] = c0;
       rw.hi[i] = c1;
       rw.start[i] = (uint32_t)st;
       rw.bit[i] = f[k0 + i];
-      atomicAdd(&rfill[(uint32_t)st / w], 1u);
+      atomicAdd(&rw.cnt[st], 1u);
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-      const uint32_t lane = threadIdx.x, c = rfill[lane];
-      uint32_t x = c;
+    // Counting sort of the keys by start slot: exclusive prefix sums of the
+    // per-slot counts (each thread a run of `per` slots), then every key takes
+    // the next place of its slot.  Inserting a region's rows in ascending
+    // start order bounds each walk by 128 slots: every stored row then spans
+    // only columns the new row's window already covers.
+    {
+      const uint32_t s0 = tid * per, s1 = s0 + per < ns ? s0 + per : ns;
+      uint32_t sum = 0;
+      for (uint32_t s = s0; s < s1; s++) sum += rw.cnt[s];
+      uint32_t x = sum;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
         if (lane >= (uint32_t)o) x += y;
       }
-      rbase[lane] = x - c;
-      if (lane == 31) rbase[kRegions] = x;
-      rfill[lane] = x - c;
+      if (lane == 31) wtot[warp] = x;
+      part[tid] = x - sum;  // exclusive within the warp
+      __syncthreads();
+      if (warp == 0) {
+        const uint32_t c = wtot[lane];
+        uint32_t y = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t z = __shfl_up_sync(0xFFFFFFFFu, y, o);
+          if (lane >= (uint32_t)o) y += z;
+        }
+        wtot[lane] = y - c;
+      }
+      __syncthreads();
+      uint32_t off = part[tid] + wtot[warp];
+      for (uint32_t s = s0; s < s1; s++) {
+        const uint32_t c = rw.cnt[s];
+        rw.cnt[s] = off;
+        off += c;
+      }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < keys; i += kRibbonThreads)
-      rw.list[atomicAdd(&rfill[rw.start[i] / w], 1u)] = i;
+    for (uint32_t i = tid; i < keys; i += kRibbonThreads) rw.list[atomicAdd(&rw.cnt[rw.start[i]], 1u)] = i;
+    __syncthreads();
+    // region g's rows (starts in [g w, (g + 1) w)) are list[rbase[g] .. rbase[g + 1]);
+    // rw.cnt[s] now holds the end of slot s
+    if (tid <= kRegions) {
+      const uint64_t s = (uint64_t)tid * w;
+      rbase[tid] = s == 0 ? 0u : (s >= ns ? keys : rw.cnt[s - 1]);
+    }
     __syncthreads();
     // phase 1: every region's own rows, in parallel
     if ((threadIdx.x & 31) == 0) {
@@ -576,8 +612,9 @@ shk_status launch_ribbon(Ctx& c, const uint64_t* lo, const uint64_t* hi, const u
     SHK_TRY(c.arena.alloc(&rows.start, n_keys));
     SHK_TRY(c.arena.alloc(&rows.list, n_keys));
     SHK_TRY(c.arena.alloc(&rows.bit, n_keys));
+    SHK_TRY(c.arena.alloc(&rows.cnt, total_slots));
     const size_t smem = ribbon128_smem(max_shard_slots);
-    if (smem <= 227 * 1024) {
+    if (smem <= 227 * 1024 - 8192) {  // beside the kernel's static shared memory
       SHK_TRY(raise_smem_limit((const void*)k_ribbon128<true>, smem));
       k_ribbon128<true><<<(unsigned)num_shards, kRibbonThreads, smem, c.stream>>>(
           lo, hi, f, K, B, S, eps_num, shard_off, band, rows, sol_words, seeds, err);
