@@ -158,6 +158,9 @@ shk_status launch_ribbon(Ctx& c, const uint64_t* lo, const uint64_t* hi, const u
                          uint64_t num_shards, const uint64_t* shard_off, uint32_t max_shard_slots,
                          uint64_t total_slots, uint64_t n_keys, uint64_t* sol_words, uint8_t* seeds,
                          uint32_t* err);
+// device scratch of the 128-bit solve (its persistent warps' sorted rows and
+// bands, per-shard state) for these shards
+shk_status ribbon128_scratch_bytes(uint64_t num_shards, uint64_t max_shard_slots, uint64_t* bytes);
 shk_status launch_max_shard_keys(Ctx& c, const uint32_t* K, uint64_t B, uint32_t S,
                                  uint64_t num_shards, uint32_t* out_max);
 // query

@@ -2,12 +2,13 @@
 // Sec. 2 Retrieval: the value is the parity of a hashed row with a segment of
 // a solution table; the table solves a nearly diagonal linear system).  A
 // standard ribbon of width 64 (leaf size n <= 24) or 128 (n > 24; Sec. 8.2's
-// 128-bit words), sharded by runs of buckets; one CTA per shard.
+// 128-bit words), sharded by runs of buckets; one CTA per shard (64-bit rows)
+// or one warp per shard (128-bit rows).
 //
-// Elimination: each key's row (start, 64-bit coefficient with bit 0 set) is
-// reduced by the row stored at its lowest set column until it reaches a free
-// column (a new pivot) or vanishes.  The stored solution is the one that is 0
-// on every non-pivot column; it does not depend on the order of the keys.
+// Elimination: each key's row (start, coefficient with bit 0 set) is reduced
+// by the row stored at its lowest set column until it reaches a free column
+// (a new pivot) or vanishes.  The stored solution is the one that is 0 on
+// every non-pivot column; it does not depend on the order of the keys.
 #include "kernels.cuh"
 
 namespace shk {
@@ -345,257 +346,418 @@ __global__ void __launch_bounds__(kRibbonThreads)
 }
 
 // ---------------------------------------------------------------------------
-// 128-bit rows (leaf size n > 24).  A shard's band (16 bytes of row and 1 byte
-// of right-hand side per slot, ~210 KB at the default ~12,000 keys) lives in
-// shared memory (SMEM) -- or, for a shard too large for it, in global scratch
-// indexed by global slot -- and the per-key rows (read once per key and
-// seed) in global scratch indexed by global key.  Every elimination step reads
-// the band, so it must be in shared memory to be fast: in global memory (L2
-// round trips) the solve was ~60x slower.  The elimination is the
-// region-parallel one of k_ribbon:
-// lane 0 of warp g eliminates the rows that start in region g, rows that step
-// past their region are parked and continue in rounds through the following
-// regions, and thread 0 finishes any rows still parked.
+// 128-bit rows (leaf size n > 24): one warp per shard.
+//
+// The keys are counting-sorted by start slot.  In ascending start order a
+// row starting at s only ever meets stored rows whose pivots lie in
+// [s, s + 127] and whose bits end at or before s + 127, so the elimination
+// needs only a window of 128 slots: slots below the current start are final
+// and go out to global memory as the window moves up.
+//
+// The window is kept reduced: no stored row has a 1 in another stored row's
+// pivot column.  Reducing a new row X then takes one step instead of a walk
+// of ~25 dependent steps: X is XORed with the stored rows at exactly the
+// pivots where X itself has a 1, and the result's lowest set column is the
+// new pivot (a free column, since the result is 0 on every pivot column).
+// The new pivot column is then cleared from the stored rows that have it.
+// These extra row operations add rows of the system to rows of the system
+// with higher pivots, so the pivot set -- and the solution that is 0 on
+// every non-pivot column -- is the one plain sequential elimination gives.
+//
+// Layout: the window is a ring of 128 slots (slot a at ring index a & 127)
+// held as 128 bit columns; lane L of the warp holds columns L, L + 32,
+// L + 64, L + 96, each 128 bits over the ring's rows.  One reduction is then
+// four column parities per lane and four ballots; occupancy and right-hand
+// sides of the ring's rows are 128-bit masks every lane holds.
 // ---------------------------------------------------------------------------
-struct Band128 {
-  uint64_t* lo;  // row bits 0..63 at its pivot slot (0: the slot is free)
-  uint64_t* hi;  // row bits 64..127
+constexpr int kRib128Warps = 2;    // warps per CTA
+constexpr uint32_t kRib128Spec = 4;  // at most this many warps per shard (seed speculation)
+
+struct Band128 {  // per slot of one warp's shard: the row in ring order (all 0: no pivot here)
+  uint4* row;
   uint8_t* rhs;
 };
-struct Rows128 {  // per key, reduced state while it is parked
-  uint64_t* lo;
-  uint64_t* hi;
-  uint32_t* start;
-  uint32_t* list;  // keys in ascending order of their start
-  uint8_t* bit;
-  uint32_t* cnt;   // per start slot (indexed by global slot): counts, then offsets
+struct Sorted128 {  // per key of one warp's shard, in ascending start order
+  uint4* row;       // the row rotated into ring order (bit c is slot start + ((c - start) & 127))
+  uint32_t* sb;     // start | orientation bit << 31
+  uint32_t* cnt;    // per start slot: counts, then offsets (aliases the band's rows)
+};
+struct Work128 {    // the persistent warps' scratch, `slots` entries each
+  uint4* row;       // [warps][slots] sorted rows
+  uint32_t* sb;
+  uint4* band;      // [warps][slots] band
+  uint8_t* rhs;
+  uint64_t slots;
+};
+struct Shard128 {   // per shard
+  uint32_t* best;   // smallest seed known to succeed (~0u: none yet)
+  uint32_t* lock;   // held while a warp writes the shard's solution bits
 };
 
-__device__ __forceinline__ int eliminate128(const Band128& bd, uint32_t* st, uint64_t* clo,
-                                            uint64_t* chi, uint8_t* bv, uint32_t limit) {
-  uint32_t s = *st;
-  uint64_t lo = *clo, hi = *chi;
-  uint8_t b = *bv;
-  for (;;) {
-    if (s >= limit) {
-      *st = s;
-      *clo = lo;
-      *chi = hi;
-      *bv = b;
-      return 2;
-    }
-    const uint64_t rl = bd.lo[s];
-    if (rl == 0) {  // a stored row has bit 0 set, so 0 marks a free slot
-      bd.lo[s] = lo;
-      bd.hi[s] = hi;
-      bd.rhs[s] = b;
-      return 1;
-    }
-    lo ^= rl;
-    hi ^= bd.hi[s];
-    b ^= bd.rhs[s];
-    if ((lo | hi) == 0) return b ? 0 : 1;
-    // bit 0 is now clear: shift the row to its next set bit (1 <= tz <= 127)
-    const uint32_t tz = lo ? ctz64(lo) : 64u + ctz64(hi);
-    if (tz >= 64) {
-      lo = hi >> (tz - 64);
-      hi = 0;
-    } else {
-      lo = (lo >> tz) | (hi << (64 - tz));
-      hi >>= tz;
-    }
-    s += tz;
+struct U128 {
+  uint64_t lo, hi;
+};
+
+__device__ __forceinline__ U128 rotl128(U128 x, uint32_t r) {  // r in 0..127
+  if (r & 64) x = U128{x.hi, x.lo};
+  r &= 63;
+  if (r == 0) return x;
+  return U128{(x.lo << r) | (x.hi >> (64 - r)), (x.hi << r) | (x.lo >> (64 - r))};
+}
+__device__ __forceinline__ U128 rotr128(U128 x, uint32_t r) { return rotl128(x, (128u - r) & 127u); }
+
+// The window's registers are indexed by 32-slot word; the word of a slot is
+// warp-uniform, so a switch on it keeps every index a compile-time constant.
+#define SHK_ON_WORD(wi, ...)              \
+  switch (wi) {                           \
+    case 0: {                             \
+      constexpr int W = 0;                \
+      __VA_ARGS__;                        \
+    } break;                              \
+    case 1: {                             \
+      constexpr int W = 1;                \
+      __VA_ARGS__;                        \
+    } break;                              \
+    case 2: {                             \
+      constexpr int W = 2;                \
+      __VA_ARGS__;                        \
+    } break;                              \
+    default: {                            \
+      constexpr int W = 3;                \
+      __VA_ARGS__;                        \
+    } break;                              \
   }
+
+__device__ __forceinline__ uint32_t first_set128(const uint32_t (&v)[4]) {  // v != 0
+  return v[0] ? __ffs((int)v[0]) - 1
+              : (v[1] ? 31 + __ffs((int)v[1]) : (v[2] ? 63 + __ffs((int)v[2]) : 95 + __ffs((int)v[3])));
 }
 
-template <class Park>
-__device__ __forceinline__ int eliminate_list128(const Band128& bd, const Rows128& rw, uint32_t t0,
-                                                 uint32_t t1, uint32_t limit, Park park) {
-  for (uint32_t t = t0; t < t1; t++) {
-    const uint32_t i = rw.list[t];
-    uint32_t st = rw.start[i];
-    uint64_t lo = rw.lo[i], hi = rw.hi[i];
-    uint8_t bv = rw.bit[i];
-    const int res = eliminate128(bd, &st, &lo, &hi, &bv, limit);
-    if (res == 0) return 0;
-    if (res == 2) {
-      rw.start[i] = st;
-      rw.lo[i] = lo;
-      rw.hi[i] = hi;
-      rw.bit[i] = bv;
-      park(i);
+// One attempt on a shard of m slots whose rows `srt` are in ascending start
+// order; the band goes to `bd`.  Returns false if the system is inconsistent.
+// Lane L holds ring columns L + 32 k (k = 0..3), each as 4 words over the
+// ring's rows (word w: rows 32 w .. 32 w + 31); occupancy and right-hand
+// sides of the ring's rows are 4 words every lane holds.
+__device__ bool solve_window128(const Sorted128& srt, uint32_t keys, uint32_t m, const Band128& bd,
+                                uint32_t lane) {
+  uint32_t col[4][4], occ[4], rhs[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    occ[k] = rhs[k] = 0;
+#pragma unroll
+    for (int w = 0; w < 4; w++) col[k][w] = 0;
+  }
+  uint32_t fin = 0;  // slots below fin are final and written out
+  // rows come in chunks of 32 (lane i holds row t0 + i), the next chunk
+  // loading while the current one is eliminated
+  uint4 a = make_uint4(0, 0, 0, 0), b = a;
+  uint32_t asb = 0, bsb = 0;
+  if (lane < keys) a = srt.row[lane], asb = srt.sb[lane];
+  if (32 + lane < keys) b = srt.row[32 + lane], bsb = srt.sb[32 + lane];
+  for (uint32_t t = 0; t <= keys; t++) {
+    if ((t & 31u) == 0 && t) {
+      a = b, asb = bsb;
+      const uint32_t i = t + 32 + lane;
+      if (i < keys) b = srt.row[i], bsb = srt.sb[i];
+    }
+    const int src = (int)(t & 31u);
+    const uint32_t x[4] = {__shfl_sync(0xFFFFFFFFu, a.x, src), __shfl_sync(0xFFFFFFFFu, a.y, src),
+                           __shfl_sync(0xFFFFFFFFu, a.z, src), __shfl_sync(0xFFFFFFFFu, a.w, src)};
+    const uint32_t sb = __shfl_sync(0xFFFFFFFFu, asb, src);
+    const uint32_t s = t < keys ? (sb & 0x7FFFFFFFu) : m;
+    // move the window up to s: slots [fin, s) are final
+    for (; fin < s; fin++) {
+      const uint32_t j = fin & 127u, jm = 1u << (j & 31u);
+      bool used = false, rb = false, p[4];
+      SHK_ON_WORD(j >> 5, {
+        used = (occ[W] & jm) != 0;
+        rb = (rhs[W] & jm) != 0;
+        _Pragma("unroll") for (int k = 0; k < 4; k++) {
+          p[k] = (col[k][W] & jm) != 0;
+          col[k][W] &= ~jm;
+        }
+        occ[W] &= ~jm;
+        rhs[W] &= ~jm;
+      });
+      uint4 row = make_uint4(0, 0, 0, 0);
+      if (used) {  // the row's ring-order words; rotated by j when read back
+        row.x = __ballot_sync(0xFFFFFFFFu, p[0]);
+        row.y = __ballot_sync(0xFFFFFFFFu, p[1]);
+        row.z = __ballot_sync(0xFFFFFFFFu, p[2]);
+        row.w = __ballot_sync(0xFFFFFFFFu, p[3]);
+      }
+      if (lane == 0) {
+        bd.row[fin] = row;
+        bd.rhs[fin] = (uint8_t)rb;
+      }
+    }
+    if (t == keys) break;
+    // reduce the new row X (ring order) in one step: XOR of the stored rows
+    // at the pivots where X has a 1
+    uint32_t y[4], R[4];
+    bool p[4];
+#pragma unroll
+    for (int w = 0; w < 4; w++) y[w] = x[w] & occ[w];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t v = (col[k][0] & y[0]) ^ (col[k][1] & y[1]) ^ (col[k][2] & y[2]) ^ (col[k][3] & y[3]);
+      p[k] = (((uint32_t)__popc(v) ^ (x[k] >> lane)) & 1u) != 0;  // X's own bit at column lane + 32 k
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) R[k] = __ballot_sync(0xFFFFFFFFu, p[k]);
+    const uint32_t bb =
+        ((sb >> 31) ^ __popc((y[0] & rhs[0]) ^ (y[1] & rhs[1]) ^ (y[2] & rhs[2]) ^ (y[3] & rhs[3]))) & 1u;
+    if ((R[0] | R[1] | R[2] | R[3]) == 0) {
+      if (bb) return false;  // dependent and inconsistent
+      continue;              // dependent and consistent: nothing to store
+    }
+    // the new pivot: R's first set ring position at or after s's, cyclically
+    const uint32_t rot = s & 127u, rm = ~0u << (rot & 31u);
+    uint32_t mk[4];
+    SHK_ON_WORD(rot >> 5, {
+      _Pragma("unroll") for (int w = 0; w < 4; w++) mk[w] = w < W ? 0u : (w == W ? R[w] & rm : R[w]);
+    });
+    const uint32_t qj = (mk[0] | mk[1] | mk[2] | mk[3]) ? first_set128(mk) : first_set128(R);
+    const uint32_t qm = 1u << (qj & 31u);
+    // column qj before the insert (the stored rows with a 1 there), plus row qj
+    uint32_t cq[4];
+    SHK_ON_WORD(qj >> 5, {
+      _Pragma("unroll") for (int w = 0; w < 4; w++) cq[w] = __shfl_sync(0xFFFFFFFFu, col[W][w], (int)(qj & 31u));
+    });
+    if (bb) {
+#pragma unroll
+      for (int w = 0; w < 4; w++) rhs[w] ^= cq[w];
+    }
+    SHK_ON_WORD(qj >> 5, {
+      cq[W] |= qm;
+      occ[W] |= qm;
+      if (bb) rhs[W] |= qm;
+    });
+    // every column c with R_c = 1: rows of column qj get R (clearing qj), row qj becomes R
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if ((R[k] >> lane) & 1u) {
+#pragma unroll
+        for (int w = 0; w < 4; w++) col[k][w] ^= cq[w];
+      }
     }
   }
-  return 1;
+  return true;
 }
 
-// Shared memory of one shard's band: lo[m] u64 | hi[m] u64 | rhs[m] u8.
-__host__ __device__ inline size_t ribbon128_smem(uint64_t m) { return (size_t)m * 17 + 16; }
+// Writes one 64-bit word of a shard's solution: plain store inside the
+// shard's bit range [p0, p1), clear-and-set on a word it shares with a
+// neighbour.
+__device__ __forceinline__ void put_word(uint64_t* sol, uint64_t gw, uint64_t bits, uint64_t p0, uint64_t p1) {
+  const uint64_t w0 = gw * 64, w1 = w0 + 64;
+  if (w0 >= p0 && w1 <= p1) {
+    sol[gw] = bits;
+    return;
+  }
+  const uint64_t lo = p0 > w0 ? p0 - w0 : 0, hi = p1 < w1 ? p1 - w0 : 64;
+  const uint64_t mask = (hi == 64 ? ~0ull : (1ull << hi) - 1) & ~((1ull << lo) - 1);
+  atomicAnd((unsigned long long*)&sol[gw], (unsigned long long)~mask);
+  atomicOr((unsigned long long*)&sol[gw], (unsigned long long)(bits & mask));
+}
 
-template <bool SMEM>
-__global__ void __launch_bounds__(kRibbonThreads)
+// Persistent warps take (shard, seed) work items in seed-major order from one
+// counter: all shards' seed 0, then seed 1 of those not yet solved, and so
+// on.  While many shards are open this is one attempt per shard at a time;
+// once fewer shards than warps are open, several seeds of a shard run at
+// once.  A warp whose seed succeeds takes the shard's lock and, if its seed
+// is still the smallest known, back-substitutes and writes the shard's bits
+// and seed; seeds are handed out in increasing order and each shard's
+// smallest success writes last, so the result is the first successful seed,
+// as in a sequential search.
+__global__ void __launch_bounds__(kRib128Warps * 32)
     k_ribbon128(const uint64_t* __restrict__ lo, const uint64_t* __restrict__ hi,
                 const uint8_t* __restrict__ f, const uint32_t* __restrict__ K, uint64_t B, uint32_t S,
-                uint32_t eps_num, const uint64_t* __restrict__ shard_off, Band128 band, Rows128 rows,
-                uint64_t* sol_words, uint8_t* seeds, uint32_t* err) {
-  extern __shared__ uint64_t band_smem[];
-  const uint64_t sh = blockIdx.x;
-  const uint64_t b0 = sh * S, b1 = b0 + S < B ? b0 + S : B;
-  const uint32_t k0 = K[b0], keys = K[b1] - K[b0];
-  const uint64_t m = shard_slots(keys, eps_num, 128);
-  if (m == 0) {
-    if (threadIdx.x == 0) seeds[sh] = 0;
-    return;
-  }
-  const uint64_t base = shard_off[sh];
-  const Band128 bd = SMEM ? Band128{band_smem, band_smem + m, (uint8_t*)(band_smem + 2 * m)}
-                          : Band128{band.lo + base, band.hi + base, band.rhs + base};
-  const Rows128 rw{rows.lo + k0, rows.hi + k0, rows.start + k0, rows.list + k0, rows.bit + k0,
-                   rows.cnt + base};
-  __shared__ int ok_s;
-  __shared__ uint32_t seed_s;
-  __shared__ uint32_t rbase[kRegions + 1], rpark[kRegions];
-  __shared__ uint32_t part[kRibbonThreads], wtot[kRegions];
-  const uint32_t w = (uint32_t)((m + kRegions - 1) / kRegions);  // region width in slots
-  const uint32_t ns = (uint32_t)(m - 127);                        // possible start slots
-  const uint32_t per = (ns + kRibbonThreads - 1) / kRibbonThreads;
-  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (uint32_t r = 0; r < kRibbonSeeds; r++) {
-    for (uint64_t i = tid; i < m; i += kRibbonThreads) bd.lo[i] = 0;
-    for (uint32_t s = tid; s < ns; s += kRibbonThreads) rw.cnt[s] = 0;
-    if (tid == 0) {
-      ok_s = 1;
-      seed_s = r;
-    }
-    __syncthreads();
-    for (uint32_t i = tid; i < keys; i += kRibbonThreads) {
-      uint64_t st, c0, c1;
-      ribbon_row(lo[k0 + i], hi[k0 + i], r, m, 128, &st, &c0, &c1);
-      rw.lo[i] = c0;
-      rw.hi[i] = c1;
-      rw.start[i] = (uint32_t)st;
-      rw.bit[i] = f[k0 + i];
-      atomicAdd(&rw.cnt[st], 1u);
-    }
-    __syncthreads();
-    // Counting sort of the keys by start slot: exclusive prefix sums of the
-    // per-slot counts (each thread a run of `per` slots), then every key takes
-    // the next place of its slot.  Inserting a region's rows in ascending
-    // start order bounds each walk by 128 slots: every stored row then spans
-    // only columns the new row's window already covers.
-    {
-      const uint32_t s0 = tid * per, s1 = s0 + per < ns ? s0 + per : ns;
-      uint32_t sum = 0;
-      for (uint32_t s = s0; s < s1; s++) sum += rw.cnt[s];
-      uint32_t x = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= (uint32_t)o) x += y;
+                uint32_t eps_num, uint64_t num_shards, const uint64_t* __restrict__ shard_off,
+                Work128 wk, uint32_t n_warps, Shard128 shd, unsigned long long* next_item,
+                unsigned long long* solved, uint64_t* sol_words, uint8_t* seeds, uint32_t* err) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t wid = blockIdx.x * kRib128Warps + (threadIdx.x >> 5);
+  if (wid >= n_warps) return;
+  const Sorted128 srt{wk.row + wid * wk.slots, wk.sb + wid * wk.slots, (uint32_t*)(wk.band + wid * wk.slots)};
+  const Band128 bd{wk.band + wid * wk.slots, wk.rhs + wid * wk.slots};
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = *(volatile unsigned long long*)solved < num_shards ? atomicAdd(next_item, 1ull) : ~0ull;
+    item = __shfl_sync(0xFFFFFFFFu, item, 0);
+    if (item >= num_shards * kRibbonSeeds) break;
+    const uint64_t sh = item % num_shards;
+    const uint32_t seed = (uint32_t)(item / num_shards);
+    if (*(volatile uint32_t*)&shd.best[sh] <= seed) continue;
+    const uint64_t b0 = sh * S, b1 = b0 + S < B ? b0 + S : B;
+    const uint32_t k0 = K[b0], keys = K[b1] - K[b0];
+    const uint32_t m = (uint32_t)shard_slots(keys, eps_num, 128);
+    bool ok = true;
+    if (m) {
+      const uint32_t ns = m - 127u;  // possible start slots
+      // counting sort of the shard's keys by start slot
+      for (uint32_t s = lane; s < ns; s += 32) srt.cnt[s] = 0;
+      __syncwarp();
+      for (uint32_t i = lane; i < keys; i += 32) {
+        uint64_t st, c0, c1;
+        ribbon_row(lo[k0 + i], hi[k0 + i], seed, m, 128, &st, &c0, &c1);
+        atomicAdd(&srt.cnt[st], 1u);
       }
-      if (lane == 31) wtot[warp] = x;
-      part[tid] = x - sum;  // exclusive within the warp
-      __syncthreads();
-      if (warp == 0) {
-        const uint32_t c = wtot[lane];
-        uint32_t y = c;
+      __syncwarp();
+      uint32_t run = 0;
+      for (uint32_t s0 = 0; s0 < ns; s0 += 128) {  // four chunks of 32 slots per round
+        uint32_t c[4], x[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const uint32_t s = s0 + 32 * j + lane;
+          c[j] = s < ns ? srt.cnt[s] : 0u;
+          x[j] = c[j];
+        }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t z = __shfl_up_sync(0xFFFFFFFFu, y, o);
-          if (lane >= (uint32_t)o) y += z;
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x[j], o);
+            if (lane >= (uint32_t)o) x[j] += y;
+          }
         }
-        wtot[lane] = y - c;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const uint32_t s = s0 + 32 * j + lane;
+          if (s < ns) srt.cnt[s] = run + x[j] - c[j];
+          run += __shfl_sync(0xFFFFFFFFu, x[j], 31);
+        }
       }
-      __syncthreads();
-      uint32_t off = part[tid] + wtot[warp];
-      for (uint32_t s = s0; s < s1; s++) {
-        const uint32_t c = rw.cnt[s];
-        rw.cnt[s] = off;
-        off += c;
+      __syncwarp();
+      for (uint32_t i0 = 0; i0 < keys; i0 += 128) {  // four keys per lane in flight
+        uint64_t st[4];
+        U128 X[4];
+        uint32_t pos[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const uint32_t i = i0 + 32 * j + lane;
+          if (i < keys) {
+            uint64_t c0, c1;
+            ribbon_row(lo[k0 + i], hi[k0 + i], seed, m, 128, &st[j], &c0, &c1);
+            X[j] = rotl128(U128{c0, c1}, (uint32_t)st[j] & 127u);
+            pos[j] = atomicAdd(&srt.cnt[st[j]], 1u);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const uint32_t i = i0 + 32 * j + lane;
+          if (i < keys) {
+            srt.row[pos[j]] = make_uint4((uint32_t)X[j].lo, (uint32_t)(X[j].lo >> 32), (uint32_t)X[j].hi,
+                                         (uint32_t)(X[j].hi >> 32));
+            srt.sb[pos[j]] = (uint32_t)st[j] | ((uint32_t)(f[k0 + i] & 1u) << 31);
+          }
+        }
+      }
+      __syncwarp();  // the band's first words held the counts
+      ok = solve_window128(srt, keys, m, bd, lane);
+      __syncwarp();
+    }
+    if (!ok) continue;
+    // the shard's lock (held only while a solution is written; bounded wait)
+    uint32_t got = 0;
+    if (lane == 0) {
+      for (uint32_t it = 0; it < (1u << 24); it++) {
+        if (atomicCAS(&shd.lock[sh], 0u, 1u) == 0u) {
+          got = 1;
+          break;
+        }
+        __nanosleep(256);
+      }
+      if (!got) atomicOr(err, kErrRibbon);
+      __threadfence();
+    }
+    got = __shfl_sync(0xFFFFFFFFu, got, 0);
+    if (!got) continue;
+    const uint32_t prev = *(volatile uint32_t*)&shd.best[sh];
+    if (seed < prev) {
+      // Back substitution from the top: x[i] = rhs[i] + parity(row[i] bits
+      // 1..127 & x[i+1 .. i+127]) on pivot slots, 0 elsewhere; the window
+      // (wlo, whi) holds x[i+1 .. i+128].  Every lane runs the recurrence;
+      // the band comes in chunks of 32 slots (lane i: slot top - i, rotated
+      // from ring order into its pivot frame), the next chunk loading
+      // meanwhile.  Lane 0 writes each finished word of the global vector.
+      const uint64_t base = shard_off[sh];
+      uint64_t wlo = 0, whi = 0, word = 0;
+      uint64_t alo = 0, ahi = 0, blo = 0, bhi = 0;
+      uint32_t ar = 0, br = 0;
+      const int64_t top = (int64_t)m - 1;
+      auto load = [&](int64_t i, uint64_t& l, uint64_t& h, uint32_t& r) {
+        l = 0, h = 0, r = 0;
+        if (i >= 0) {
+          const uint4 q = bd.row[i];
+          const U128 v = rotr128(U128{q.x | ((uint64_t)q.y << 32), q.z | ((uint64_t)q.w << 32)}, (uint32_t)i & 127u);
+          l = v.lo, h = v.hi, r = bd.rhs[i];
+        }
+      };
+      load(top - (int64_t)lane, alo, ahi, ar);
+      load(top - 32 - (int64_t)lane, blo, bhi, br);
+      for (int64_t c0 = top; c0 >= 0; c0 -= 32) {
+        const int n = c0 >= 31 ? 32 : (int)c0 + 1;
+        for (int u = 0; u < n; u++) {
+          const int64_t i = c0 - u;
+          const uint64_t rl = __shfl_sync(0xFFFFFFFFu, alo, u), rh = __shfl_sync(0xFFFFFFFFu, ahi, u);
+          const uint32_t rr = __shfl_sync(0xFFFFFFFFu, ar, u);
+          uint64_t v = 0;
+          if (rl) {
+            const uint64_t slo = (rl >> 1) | (rh << 63), shi = rh >> 1;
+            v = (uint64_t)((rr ^ __popcll(slo & wlo) ^ __popcll(shi & whi)) & 1u);
+          }
+          whi = (whi << 1) | (wlo >> 63);
+          wlo = (wlo << 1) | v;
+          const uint64_t p = base + (uint64_t)i;
+          word |= v << (p & 63);
+          if ((p & 63) == 0 || i == 0) {
+            if (lane == 0) put_word(sol_words, p >> 6, word, base, base + m);
+            word = 0;
+          }
+        }
+        alo = blo, ahi = bhi, ar = br;
+        load(c0 - 64 - (int64_t)lane, blo, bhi, br);
+      }
+      if (lane == 0) {
+        seeds[sh] = (uint8_t)seed;
+        shd.best[sh] = seed;
+        if (prev == ~0u) atomicAdd(solved, 1ull);
       }
     }
-    __syncthreads();
-    for (uint32_t i = tid; i < keys; i += kRibbonThreads) rw.list[atomicAdd(&rw.cnt[rw.start[i]], 1u)] = i;
-    __syncthreads();
-    // region g's rows (starts in [g w, (g + 1) w)) are list[rbase[g] .. rbase[g + 1]);
-    // rw.cnt[s] now holds the end of slot s
-    if (tid <= kRegions) {
-      const uint64_t s = (uint64_t)tid * w;
-      rbase[tid] = s == 0 ? 0u : (s >= ns ? keys : rw.cnt[s - 1]);
+    if (lane == 0) {
+      __threadfence();
+      atomicExch(&shd.lock[sh], 0u);
     }
-    __syncthreads();
-    // phase 1: every region's own rows, in parallel
-    if ((threadIdx.x & 31) == 0) {
-      const uint32_t g = threadIdx.x >> 5;
-      const uint32_t r1 = (g + 1) * w < m ? (g + 1) * w : (uint32_t)m;
-      const uint32_t t0 = rbase[g], t1 = rbase[g + 1];
-      uint32_t np = t0;
-      const int ok = eliminate_list128(bd, rw, t0, t1, r1, [&](uint32_t i) { rw.list[np++] = i; });
-      rpark[g] = np - t0;
-      if (!ok) ok_s = 0;
-    }
-    __syncthreads();
-    // phase 2: parked rows continue through the following regions in rounds
-    // (in round t region g's rows walk region g + 1 + t; no two warps share a
-    // region in a round), then thread 0 finishes what is left
-    const uint32_t g = threadIdx.x >> 5;
-    const bool leader = (threadIdx.x & 31) == 0;
-    int pending = __syncthreads_or(leader && rpark[g] != 0);
-    for (uint32_t round = 0; pending && ok_s && round < kRegions; round++) {
-      if (leader && rpark[g] != 0) {
-        const uint32_t end = g + 2 + round;
-        const uint32_t lim = end < kRegions ? end * w : 0xFFFFFFFFu;
-        uint32_t keep = 0;
-        const int ok = eliminate_list128(bd, rw, rbase[g], rbase[g] + rpark[g], lim,
-                                         [&](uint32_t i) { rw.list[rbase[g] + keep++] = i; });
-        rpark[g] = keep;
-        if (!ok) ok_s = 0;
-      }
-      pending = __syncthreads_or(leader && rpark[g] != 0);
-    }
-    if (threadIdx.x == 0 && ok_s && pending) {
-      int ok = 1;
-      for (uint32_t h = 0; h < kRegions && ok; h++)
-        ok = eliminate_list128(bd, rw, rbase[h], rbase[h] + rpark[h], 0xFFFFFFFFu, [](uint32_t) {});
-      ok_s = ok;
-    }
-    __syncthreads();
-    if (ok_s) break;
-    __syncthreads();
+    __syncwarp();
   }
-  if (!ok_s) {
-    if (threadIdx.x == 0) atomicOr(err, kErrRibbon);
-    return;
-  }
-  if (threadIdx.x != 0) return;
-  seeds[sh] = (uint8_t)seed_s;
-  // Back substitution from the top: x[i] = rhs[i] + parity(row[i] bits
-  // 1..127 & x[i+1 .. i+127]) on pivot slots, 0 elsewhere; the window
-  // (wlo, whi) holds x[i+1 .. i+128].  Finished 64-bit words of the shard's
-  // bits are ORed into the global vector at the shard's bit offset.
-  uint64_t wlo = 0, whi = 0, word = 0;
-  for (int64_t i = (int64_t)m - 1; i >= 0; i--) {
-    uint64_t v = 0;
-    const uint64_t rl = bd.lo[i];
-    if (rl) {
-      const uint64_t rh = bd.hi[i];
-      const uint64_t slo = (rl >> 1) | (rh << 63), shi = rh >> 1;
-      v = (uint64_t)((bd.rhs[i] ^ __popcll(slo & wlo) ^ __popcll(shi & whi)) & 1);
-    }
-    whi = (whi << 1) | (wlo >> 63);
-    wlo = (wlo << 1) | v;
-    word |= v << (i & 63);
-    if ((i & 63) == 0) {
-      if (word) {
-        const uint64_t p = base + (uint64_t)i;
-        const uint32_t s = (uint32_t)(p & 63);
-        atomicOr((unsigned long long*)&sol_words[p >> 6], (unsigned long long)(word << s));
-        if (s && (word >> (64 - s)))
-          atomicOr((unsigned long long*)&sol_words[(p >> 6) + 1], (unsigned long long)(word >> (64 - s)));
-      }
-      word = 0;
-    }
-  }
+}
+
+__global__ void k_ribbon128_check(const unsigned long long* solved, uint64_t num_shards, uint32_t* err) {
+  if (*solved < num_shards) atomicOr(err, kErrRibbon);
+}
+
+// Persistent warps for the 128-bit solve: those resident at once, at most
+// kRib128Spec per shard.
+static shk_status ribbon128_warps(uint64_t num_shards, uint32_t* out) {
+  int dev = 0, sms = 0, per_sm = 0;
+  SHK_CUDA(cudaGetDevice(&dev));
+  SHK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SHK_TRY(blocks_per_sm((const void*)k_ribbon128, kRib128Warps * 32, 0, &per_sm));
+  const uint64_t resident = (uint64_t)sms * (per_sm > 0 ? per_sm : 1) * kRib128Warps;
+  const uint64_t want = num_shards * kRib128Spec;
+  *out = (uint32_t)(want < resident ? want : resident);
+  return SHK_OK;
+}
+
+// Scratch bytes per persistent warp and slot: sorted rows (16 + 4 per key, at
+// most one key per slot) and the band (16 + 1).
+constexpr uint64_t kRib128BytesPerSlot = 37;
+
+shk_status ribbon128_scratch_bytes(uint64_t num_shards, uint64_t max_shard_slots, uint64_t* bytes) {
+  uint32_t w = 0;
+  SHK_TRY(ribbon128_warps(num_shards, &w));
+  *bytes = (uint64_t)w * max_shard_slots * kRib128BytesPerSlot + num_shards * 8 + 64;
+  return SHK_OK;
 }
 
 shk_status launch_ribbon(Ctx& c, const uint64_t* lo, const uint64_t* hi, const uint8_t* f,
@@ -605,27 +767,31 @@ shk_status launch_ribbon(Ctx& c, const uint64_t* lo, const uint64_t* hi, const u
                          uint32_t* err) {
   if (num_shards == 0) return SHK_OK;
   if (w == 128) {
-    Band128 band{nullptr, nullptr, nullptr};
-    Rows128 rows;
-    SHK_TRY(c.arena.alloc(&rows.lo, n_keys));
-    SHK_TRY(c.arena.alloc(&rows.hi, n_keys));
-    SHK_TRY(c.arena.alloc(&rows.start, n_keys));
-    SHK_TRY(c.arena.alloc(&rows.list, n_keys));
-    SHK_TRY(c.arena.alloc(&rows.bit, n_keys));
-    SHK_TRY(c.arena.alloc(&rows.cnt, total_slots));
-    const size_t smem = ribbon128_smem(max_shard_slots);
-    if (smem <= 227 * 1024 - 8192) {  // beside the kernel's static shared memory
-      SHK_TRY(raise_smem_limit((const void*)k_ribbon128<true>, smem));
-      k_ribbon128<true><<<(unsigned)num_shards, kRibbonThreads, smem, c.stream>>>(
-          lo, hi, f, K, B, S, eps_num, shard_off, band, rows, sol_words, seeds, err);
-    } else {  // a shard too large for shared memory: the band in global scratch
-      SHK_TRY(c.arena.alloc(&band.lo, total_slots));
-      SHK_TRY(c.arena.alloc(&band.hi, total_slots));
-      SHK_TRY(c.arena.alloc(&band.rhs, total_slots));
-      k_ribbon128<false><<<(unsigned)num_shards, kRibbonThreads, 0, c.stream>>>(
-          lo, hi, f, K, B, S, eps_num, shard_off, band, rows, sol_words, seeds, err);
-    }
-    c.launches++;
+    // starts and the orientation bit share a 32-bit word
+    if (max_shard_slots >= 0x80000000u) return fail(SHK_EINVAL, "retrieval shard too large");
+    uint32_t nw = 0;
+    SHK_TRY(ribbon128_warps(num_shards, &nw));
+    Work128 wk;
+    wk.slots = max_shard_slots;
+    const uint64_t cells = (uint64_t)nw * max_shard_slots;
+    SHK_TRY(c.arena.alloc(&wk.row, cells));
+    SHK_TRY(c.arena.alloc(&wk.sb, cells));
+    SHK_TRY(c.arena.alloc(&wk.band, cells));
+    SHK_TRY(c.arena.alloc(&wk.rhs, cells));
+    Shard128 shd;
+    unsigned long long* ctr;
+    SHK_TRY(c.arena.alloc(&shd.best, num_shards));
+    SHK_TRY(c.arena.alloc(&shd.lock, num_shards));
+    SHK_TRY(c.arena.alloc(&ctr, 2));
+    SHK_CUDA(cudaMemsetAsync(shd.best, 0xFF, num_shards * 4, c.stream));
+    SHK_CUDA(cudaMemsetAsync(shd.lock, 0, num_shards * 4, c.stream));
+    SHK_CUDA(cudaMemsetAsync(ctr, 0, 16, c.stream));
+    const uint32_t blocks = (nw + kRib128Warps - 1) / kRib128Warps;
+    k_ribbon128<<<blocks, kRib128Warps * 32, 0, c.stream>>>(lo, hi, f, K, B, S, eps_num, num_shards,
+                                                            shard_off, wk, nw, shd, ctr, ctr + 1,
+                                                            sol_words, seeds, err);
+    k_ribbon128_check<<<1, 1, 0, c.stream>>>(ctr + 1, num_shards, err);
+    c.launches += 2;
     SHK_CUDA(cudaGetLastError());
     return SHK_OK;
   }

@@ -51,14 +51,25 @@ __global__ void k_rebase(uint64_t* o, uint64_t n, uint64_t base) {
 // Device bytes a build holds while it runs: keys staged on the device, three
 // 16-byte fingerprint copies (hashed, partitioned once and twice), the leaf
 // order copy (lo, hi), orientation bytes, per-leaf arrays (up to ~30 bytes a
-// key at the smallest leaves), the 128-bit retrieval solver's per-key rows
-// (25 bytes a key, up to 42 with an oversized shard's band), per-bucket
-// arrays, the encoded result; plus a fixed allowance.
+// key at the smallest leaves), per-bucket arrays, the encoded result, a fixed
+// allowance; and with 128-bit retrieval rows the solver's scratch: its
+// persistent warps' rows and bands, sized for a shard of 1.25 times the
+// average shard's keys plus 512.
 uint64_t footprint(uint64_t n_keys, const shk_build_opts& o, uint64_t key_bytes) {
   const uint64_t b = o.bucket_size ? o.bucket_size : 1;
   const uint64_t buckets = n_keys / b + 1;
-  const uint64_t per_key = shk::ribbon_width(o.leaf_size) == 128 ? 112 : 96;
-  return key_bytes + n_keys * per_key + buckets * 96 + (8ull << 20);
+  uint64_t bytes = key_bytes + n_keys * 96 + buckets * 96 + (8ull << 20);
+  const uint32_t rw = shk::ribbon_width(o.leaf_size);
+  if (rw == 128 && n_keys) {
+    const uint64_t S = o.shard_buckets ? o.shard_buckets : shk::default_shard_buckets((uint32_t)b, rw);
+    const uint64_t shards = (buckets + S - 1) / S;
+    const uint32_t eps = o.eps_num ? o.eps_num : shk::default_eps_num(rw);
+    uint64_t keys = n_keys / shards + n_keys / shards / 4 + 512;
+    if (keys > n_keys) keys = n_keys;
+    uint64_t scratch = 0;
+    if (shk::ribbon128_scratch_bytes(shards, shk::shard_slots(keys, eps, rw), &scratch) == SHK_OK) bytes += scratch;
+  }
+  return bytes;
 }
 
 }  // namespace
