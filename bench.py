@@ -457,6 +457,9 @@ def run_ours(args):
         "u64_1M_leaf48": u64rec,
         "served_builds": {} if args.no_subrecords else serve_run(pkg, args.serve_requests, args.serve_max_keys,
                                                                   True, rank),
+        "served_builds_burst": {} if args.no_subrecords else serve_run(pkg, args.serve_requests,
+                                                                        args.serve_max_keys, True, rank,
+                                                                        burst=True),
     }
     if clocks:
         line["clocks"] = clocks
@@ -565,7 +568,7 @@ def run_leafbatch(args):
 
 
 def serve_run(pkg, requests: int, max_keys: float, rf: bool, rank: int = 0, check_alone: bool = True,
-              clk=None) -> dict:
+              clk=None, burst: bool = False) -> dict:
     """Served builds: a Poisson stream of MPHF build requests (uniform u64
     keys generated on the device, sizes log-uniform in [1e3, max_keys], leaf
     size 48 or 58 by coin, bucket 2000, stream seed 5, request i from sub-seed
@@ -574,7 +577,9 @@ def serve_run(pkg, requests: int, max_keys: float, rf: bool, rank: int = 0, chec
     ~80 % offered load from a calibration build of each leaf size.  Reports
     p50/p99 build latency (submit to finish), aggregate keys/s, how the
     requests' leaf-search kernels overlapped on the device (device-time
-    intervals), and whether every result equals the same build alone."""
+    intervals), and whether every result equals the same build alone.  With
+    burst, every request arrives at once (a backlog: the server's throughput
+    and its builds' overlap on the device)."""
     import torch
 
     import shk_inputs
@@ -598,6 +603,8 @@ def serve_run(pkg, requests: int, max_keys: float, rf: bool, rank: int = 0, chec
     service = float(np.mean([k.numel() * per_key[n] for k, n in reqs]))
     rate = 0.8 / service
     gaps = -np.log(1.0 - shk_inputs.uniform01(55 + 1000 * rank, R)) / rate
+    if burst:
+        gaps = np.zeros(R)
     srv = pkg.shk_server_create(0, 4)
     pending, infos, blobs, spans = {}, {}, {}, []
 
@@ -635,7 +642,8 @@ def serve_run(pkg, requests: int, max_keys: float, rf: bool, rank: int = 0, chec
     overlapping = sum(1 for j, (a, b) in enumerate(spans) if any(a < d and c < b for c, d in spans[:j]))
     rec = {"workload": "served_builds_poisson", "requests": R, "sizes": f"log-uniform [1e3, {max_keys:.0e}]",
            "leaf_sizes": [48, 58], "leaf_mode": "rf" if rf else "plain", "bucket_size": BUCKET,
-           "offered_load": 0.8, "workers": 4, "keys_submitted_as": "device tensors (kept on the device)",
+           "offered_load": "all at once" if burst else 0.8, "workers": 4,
+           "keys_submitted_as": "device tensors (kept on the device)",
            "keys_per_s": total / span, "p50_ms": float(np.percentile(lat, 50)),
            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "all_ok": ok,
            "total_keys": total, "makespan_s": span, "arrival_rate_per_s": rate,
