@@ -439,8 +439,10 @@ def run_ours(args):
         "leaf_seeds_per_s": st["leaf_seeds_tested"] / (leaf_ms / 1e3),
         "leaf_candidates_per_s": st["leaf_seeds_min"] / (leaf_ms / 1e3),
         "leaf_hash_evals_per_s": st["leaf_hash_evals"] / (leaf_ms / 1e3),
+        "leaf_seeds_executed_over_tested": st["leaf_seeds_executed"] / max(st["leaf_seeds_tested"], 1),
         "leaf_note": "seeds tested = sum over leaves of floor(v/m) + 1 (rotation fitting; seed + 1 plain); "
-                     "candidates = sum of (v + 1), v = seed m + rotation",
+                     "candidates = sum of (v + 1), v = seed m + rotation; executed / tested = the work "
+                     "stealing's overshoot (seeds past a leaf's solution searched by helper warps)",
         "phase_ms": {k: float(np.mean([s[k] for s in stats])) for k in
                      ("ms_fingerprint", "ms_partition", "ms_split", "ms_leaf", "ms_orient", "ms_encode",
                       "ms_ribbon", "ms_total")},
