@@ -501,18 +501,24 @@ shk_status tuned_leaf_cfg(Ctx& c, uint32_t m, LeafCfg* out) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   TuneSlot& slot = g_tune[c.device][bin];
   if (!slot.done) {
-    // Every configuration at its best of 3 probe launches.  Among those within
-    // 1 % of the best rate the one with the fewest warps per block is taken:
-    // in a build, smaller blocks leave less SM time idle while the last
-    // leaves finish (measured on 10^6-key builds: 8- and 4-warp blocks 3 %
-    // faster than 16-warp blocks of nearly the same probe rate).
+    // Every configuration at its best of 3 probe launches.  The probe's short
+    // searches overrate 16-warp blocks by 2-3 % against real builds, where
+    // 8-warp blocks were fastest in every sweep (10^6 keys, n = 48: 4/8/4
+    // 268.0 ms, 4/4/2 271.5, 4/16/2 272.0, though 4/16/2 probed 2.3 % above
+    // 4/8/4): the fastest 8-warp configuration within 3 % of the best rate is
+    // taken; failing that, among those within 1 % the one with the fewest
+    // warps per block (smaller blocks leave less SM time idle while the last
+    // leaves finish).
     double rate[kNumLeafCfg], top = 0;
     for (int i = 0; i < kNumLeafCfg; i++) {
       SHK_TRY(probe_leaf_cfg(c, kLeafTable[i].cfg, rep, &rate[i], 3));
       top = std::max(top, rate[i]);
     }
     int pick = -1;
-    for (int i = 0; i < kNumLeafCfg; i++) {
+    for (int i = 0; i < kNumLeafCfg; i++)
+      if (kLeafTable[i].cfg.warps == 8 && rate[i] >= 0.97 * top && (pick < 0 || rate[i] > rate[pick])) pick = i;
+    const bool have8 = pick >= 0;
+    for (int i = 0; !have8 && i < kNumLeafCfg; i++) {
       if (rate[i] < 0.99 * top) continue;
       if (pick < 0 || kLeafTable[i].cfg.warps < kLeafTable[pick].cfg.warps ||
           (kLeafTable[i].cfg.warps == kLeafTable[pick].cfg.warps && rate[i] > rate[pick]))
