@@ -319,7 +319,7 @@ shk_status shk_server_cancel(shk_server* srv, uint64_t req_id);
  * staged, 96 bytes per key, 96 per bucket and 8 MiB; with leaf size above 24
  * also the 128-bit retrieval solver's scratch (37 bytes per slot of a shard
  * of 1.25 times the average shard's keys plus 512, for each of its persistent
- * warps: those resident on the device, at most 4 per shard).  A build that runs
+ * warps: those resident on the device, at most 8 per shard).  A build that runs
  * alone reports its measured peak in shk_stats.device_bytes_peak. */
 shk_status shk_build_footprint(const shk_keys* keys, const shk_build_opts* opts, uint64_t* bytes);
 

@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kRibbonThreads)
 // sides of the ring's rows are 128-bit masks every lane holds.
 // ---------------------------------------------------------------------------
 constexpr int kRib128Warps = 2;    // warps per CTA
-constexpr uint32_t kRib128Spec = 4;  // at most this many warps per shard (seed speculation)
+constexpr uint32_t kRib128Spec = 8;  // at most this many warps per shard (seed speculation)
 
 struct Band128 {  // per slot of one warp's shard: the row in ring order (all 0: no pivot here)
   uint4* row;
@@ -434,12 +434,13 @@ __device__ __forceinline__ uint32_t first_set128(const uint32_t (&v)[4]) {  // v
 }
 
 // One attempt on a shard of m slots whose rows `srt` are in ascending start
-// order; the band goes to `bd`.  Returns false if the system is inconsistent.
+// order; the band goes to `bd`.  Returns false if the system is inconsistent
+// or a seed below `seed` has succeeded meanwhile (*best).
 // Lane L holds ring columns L + 32 k (k = 0..3), each as 4 words over the
 // ring's rows (word w: rows 32 w .. 32 w + 31); occupancy and right-hand
 // sides of the ring's rows are 4 words every lane holds.
 __device__ bool solve_window128(const Sorted128& srt, uint32_t keys, uint32_t m, const Band128& bd,
-                                uint32_t lane) {
+                                uint32_t lane, const uint32_t* best, uint32_t seed) {
   uint32_t col[4][4], occ[4], rhs[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) {
@@ -456,6 +457,13 @@ __device__ bool solve_window128(const Sorted128& srt, uint32_t keys, uint32_t m,
   if (32 + lane < keys) b = srt.row[32 + lane], bsb = srt.sb[32 + lane];
   for (uint32_t t = 0; t <= keys; t++) {
     if ((t & 31u) == 0 && t) {
+      // a smaller seed of this shard has succeeded meanwhile: this attempt
+      // cannot be the result (checked every 1024 keys)
+      if ((t & 1023u) == 0) {
+        uint32_t stop = 0;
+        if (lane == 0) stop = *(const volatile uint32_t*)best <= seed;
+        if (__shfl_sync(0xFFFFFFFFu, stop, 0)) return false;
+      }
       a = b, asb = bsb;
       const uint32_t i = t + 32 + lane;
       if (i < keys) b = srt.row[i], bsb = srt.sb[i];
@@ -536,10 +544,9 @@ __device__ bool solve_window128(const Sorted128& srt, uint32_t keys, uint32_t m,
     // every column c with R_c = 1: rows of column qj get R (clearing qj), row qj becomes R
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      if ((R[k] >> lane) & 1u) {
+      const uint32_t sel = 0u - ((R[k] >> lane) & 1u);  // all ones where R has column lane + 32 k
 #pragma unroll
-        for (int w = 0; w < 4; w++) col[k][w] ^= cq[w];
-      }
+      for (int w = 0; w < 4; w++) col[k][w] ^= cq[w] & sel;
     }
   }
   return true;
@@ -653,7 +660,7 @@ __global__ void __launch_bounds__(kRib128Warps * 32)
         }
       }
       __syncwarp();  // the band's first words held the counts
-      ok = solve_window128(srt, keys, m, bd, lane);
+      ok = solve_window128(srt, keys, m, bd, lane, &shd.best[sh], seed);
       __syncwarp();
     }
     if (!ok) continue;
