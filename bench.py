@@ -704,6 +704,22 @@ def run_u64(args):
     global N_KEYS
     N_KEYS = args.keys or N_KEYS
     rec, _ = u64_subrecord(pkg, args, flush, torch.cuda.current_stream(), peak, cfg)
+    if args.oracle_full:
+        # cpu_baseline leg: the oracle's whole build of the same keys on every
+        # host core, and its bytes against the GPU build's
+        import shk_inputs
+
+        import oracle
+
+        keys = shk_inputs.distinct_u64(N_KEYS, KEY_SEED)
+        gpu_blob = pkg.shk_build(keys, LEAF, BUCKET).serialize()
+        cores = os.cpu_count() or 1
+        t = time.perf_counter()
+        orc_blob = oracle.build_mphf(keys, n=LEAF, b=BUCKET, nthreads=cores)
+        orc_s = time.perf_counter() - t
+        rec["cpu_baseline_full"] = {"value": N_KEYS / orc_s, "unit": "keys/s", "cores": cores, "kind": "oracle",
+                                    "seconds": orc_s, "sample": "the whole workload (all keys, all leaves)",
+                                    "bytes_equal_to_gpu_build": orc_blob == gpu_blob}
     print(json.dumps(rec), flush=True)
     return 0
 
@@ -723,6 +739,8 @@ def main():
     ap.add_argument("--parity-leaves", type=int, default=64, help="oracle leg: leaves compared")
     ap.add_argument("--keys", type=int, default=None,
                     help="key (leafbatch: leaf) count other than the workload's own, for profiling runs")
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="workload u64: also time the oracle's whole build of the same keys on all host cores")
     ap.add_argument("--compare-per-bucket", action="store_true",
                     help="time the one-launch-per-bucket form on all 10^6 keys (slow)")
     ap.add_argument("--leaf-cfg", default="",
