@@ -45,7 +45,7 @@ OPS_PER_EVAL_NARROW = 9
 # AND it into the seed's rotation set (one op, a three-input AND taking two
 # cells per word)
 OPS_PER_RF_CELL = 3
-LEAF_TRAFFIC_PER_LEAF = 920_576 / 2_100  # DRAM bytes per leaf of the plain leaf kernel, ncu
+LEAF_TRAFFIC_PER_LEAF = 926_208 / 2_100  # DRAM bytes per leaf of the plain leaf kernel, ncu
 
 
 def _peaks():
