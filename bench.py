@@ -220,6 +220,19 @@ def _int_issue(pkg):
     return out
 
 
+def _radix_rec(stats, count):
+    """The radix partition phase alone: two passes that each read and write
+    the 16-byte fingerprint record of every key (32 B per key per pass
+    counted once read and once written) against the measured copy
+    bandwidth."""
+    ms = float(np.mean([s["ms_partition"] for s in stats]))
+    gbs = 2 * 32 * count / (ms / 1e3) / 1e9
+    peak = float(_peaks().get("hbm_gbs", 6800.0))
+    return {"ms": ms, "passes": 2, "algorithmic_bytes": 2 * 32 * count, "achieved_gbs": gbs, "peak_gbs": peak,
+            "frac": gbs / peak, "note": "phase time includes the host's check of the histogram and the "
+                                        "launch gaps; ncu per-pass figures in profiles/"}
+
+
 def u64_subrecord(pkg, args, flush, stream, peak_tops, cfg):
     """The 10^6 distinct u64 keys (stream seed 2), leaf 48, bucket 2000 build:
     plain leaves (with the plain leaf kernel's roofline), the same keys with
@@ -450,6 +463,7 @@ def run_ours(args):
                      ("ms_fingerprint", "ms_partition", "ms_split", "ms_leaf", "ms_orient", "ms_encode",
                       "ms_ribbon", "ms_total")},
         "partition_gbs": part_bytes / (part_ms / 1e3) / 1e9,
+        "radix_partition": _radix_rec(stats, count),
         "roofline": roofline,
         "int_issue_microbench": ints,
         "e2e": {"value": count * ws / e2e_s, "unit": "keys/s", "h2d_bytes_per_step":

@@ -86,8 +86,11 @@ typedef enum {
 typedef struct {
   uint32_t leaf_size;        /* n, 2..64 (leaf bit mask is one 64-bit word)      */
   uint32_t bucket_size;      /* b, n..4096: expected keys per bucket            */
-  uint32_t shard_buckets;    /* retrieval shard = this many buckets; 0 = 8192/b  */
-  uint32_t eps_num;          /* retrieval overhead eps = eps_num/65536; 0 = 3277 */
+  uint32_t shard_buckets;    /* retrieval shard = this many buckets; 0 = the     */
+                             /* default: 12288/b (leaf size > 24: 128-bit rows), */
+                             /* 8192/b (64-bit rows), at least 1                 */
+  uint32_t eps_num;          /* retrieval overhead eps = eps_num/65536; 0 = the  */
+                             /* default: 66 (128-bit rows), 3277 (64-bit rows)   */
   uint32_t sched;            /* shk_sched                                        */
   uint32_t seeds_per_lane;   /* leaf kernel: seeds per lane per pass (1, 2, 4);  */
                              /* 0 = the autotuner's choice for this leaf size     */
