@@ -274,6 +274,9 @@ def u64_subrecord(pkg, args, flush, stream, peak_tops, cfg):
                         "traffic": LEAF_TRAFFIC_PER_LEAF * stats[-1]["n_leaves"],
                         "traffic_note": "scaled by leaves from an ncu capture of the 10^5-key build",
                         "ops_per_launch": evals * OPS_PER_EVAL_WIDE}}
+    core = pkg.shk_int_issue_rate(3, 256)[0]
+    rec["roofline"]["frac_of_hash_core"] = evals / (leaf_ms / 1e3) / core
+    rec["roofline"]["hash_core_evals_per_s"] = core
     # rotation fitting with partial hash calculation on the same keys
     rf = []
     for _ in range(3):
@@ -431,7 +434,11 @@ def run_ours(args):
                 "peak_note": f"{sms} SMs x 4 schedulers x 32 lanes x {sm_max_mhz:.0f} MHz (max SM clock); "
                              f"measured achievable on this GPU (1:1 multiply-add + logic): "
                              f"{ints['imad_plus_lop3']:.1f}",
-                "frac_of_measured_achievable": achieved / ints["imad_plus_lop3"]}
+                "frac_of_measured_achievable": achieved / ints["imad_plus_lop3"],
+                "hash_evals_per_s": st["leaf_hash_evals"] / (leaf_ms / 1e3),
+                "frac_of_hash_core": st["leaf_hash_evals"] / (leaf_ms / 1e3) / ints["leaf_hash_evals"],
+                "hash_core_note": "hash evaluations/s over the bare leaf hash core's (keys in registers, "
+                                  "int_issue_microbench.leaf_hash_evals): the rate the hash alone allows"}
     cfg = {}
     if args.leaf_cfg:
         u, w, r = (int(v) for v in args.leaf_cfg.split(","))
