@@ -404,6 +404,18 @@ def test_retrieval_overhead_option(pkg, orc, eps):
         m.close()
 
 
+@pytest.mark.parametrize("S,eps", [(1, 0), (16, 655), (0, 16), (0, 655)])
+def test_128bit_retrieval_options(pkg, orc, S, eps):
+    """128-bit retrieval rows (leaf size 32): shards of one bucket, shards of
+    ~32,000 keys at eps = 1 %, and default shards at eps = 0.024 % and 1 %.
+    The shards need different numbers of seeds, run on the persistent warps'
+    speculative (shard, seed) items.  Every build equals the oracle's bytes."""
+    keys = inp.distinct_u64(50000, 700 + S + eps)
+    m = pkg.shk_build(_dev(keys), 32, 2000, shard_buckets=S, eps_num=eps, leaf_mode=1)
+    assert m.serialize() == orc.build_mphf(keys, n=32, b=2000, shard_buckets=S, eps_num=eps, leaf_mode=1)
+    m.close()
+
+
 def test_string_keys_leaf64_rotation_fitting_sampled(pkg, orc):
     """The 10^8-string workload's parameters on 2 * 10^5 strings (lengths
     10..50, bytes 1..127, stream seed 4): n = 64, b = 2000, rotation fitting,
