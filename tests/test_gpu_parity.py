@@ -182,6 +182,34 @@ def test_empty_and_errors(pkg, orc):
     assert pkg.shk_build(_dev(k2), 16, 100).serialize() == orc.build_mphf(k2, n=16, b=100)
 
 
+@pytest.mark.parametrize("leaf_mode", [0, 1])
+def test_tiny_builds_and_an_empty_shard_with_128bit_rows(pkg, orc, leaf_mode):
+    """Leaf size 32 (128-bit retrieval rows): 1, 2, 3 and 33 keys, and a
+    build whose middle bucket -- a shard of its own -- holds no key (128-bit
+    fingerprints placed in buckets 0 and 2 of 3), equal the oracle's bytes
+    and query to a bijection."""
+    for N in (1, 2, 3, 33):
+        keys = inp.distinct_u64(N, 800 + N)
+        m = pkg.shk_build(_dev(keys), 32, 2000, leaf_mode=leaf_mode)
+        want = orc.build_mphf(keys, n=32, b=2000, leaf_mode=leaf_mode)
+        assert m.serialize() == want, N
+        r = np.sort(m.query(_dev(keys)).cpu().numpy().view(np.uint64))
+        assert np.array_equal(r, np.arange(N, dtype=np.uint64))
+        m.close()
+    # 65 keys, b = 32: B = 3 buckets; bucket = floor(hi * 3 / 2^64)
+    lo = inp.splitmix64_stream(810, 65)
+    u = inp.splitmix64_stream(811, 65) >> np.uint64(2)  # below 2^62
+    third = np.uint64(2**64 // 3)
+    hi = np.where(np.arange(65) < 33, u, u + np.uint64(2) * third)  # bucket 0 (hi < 2^62 < 2^64/3) or 2
+    fp = np.stack([lo, hi], axis=1).copy().reshape(-1)
+    m = pkg.shk_build(_dev(fp), 32, 32, kind=pkg.SHK_KEYS_FP128, shard_buckets=1, leaf_mode=leaf_mode)
+    want = orc.build_mphf(kind=orc.KEYS_FP128, fp=fp, n=32, b=32, shard_buckets=1, leaf_mode=leaf_mode)
+    assert m.serialize() == want
+    assert np.array_equal(np.sort(m.query(_dev(fp), kind=pkg.SHK_KEYS_FP128).cpu().numpy().view(np.uint64)),
+                          np.arange(65, dtype=np.uint64))
+    m.close()
+
+
 def test_deserialize_oracle_bytes(pkg, orc):
     keys = inp.distinct_u64(12000, 11)
     blob = orc.build_mphf(keys, n=36, b=1500)
