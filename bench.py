@@ -618,7 +618,11 @@ def run_leafbatch(args):
             "key_seed_evals_per_s": evals * args.steps / t, "mean_seed": float(s.mean()),
             "graph_replays": pkg.shk_leaf_graph_replays() - r0,
             "roofline": {"bound": "alu", "kernel": kernel, "achieved": ach, "peak": peak,
-                         "unit": "T int-lane-ops/s", "frac": ach / peak}}
+                         "unit": "T int-lane-ops/s", "frac": ach / peak,
+                         "ops_note": ("hash evaluations only (expected |B| per seed, |A| per 8 seeds); the "
+                                      "rotation filter's work is not counted, so a lower bound (the build "
+                                      "record counts it)") if rf else
+                                     f"{OPS_PER_EVAL_WIDE} per key-seed evaluation, sum over leaves of (seed + 1) m"}}
     if not rf:
         line["tuned_cfg"] = pkg.shk_leaf_tune(64)
     clocks = clk.summary()
