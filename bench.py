@@ -640,7 +640,8 @@ def serve_run(pkg, requests: int, max_keys: float, rf: bool, rank: int = 0, chec
     size 48 or 58 by coin, bucket 2000, stream seed 5, request i from sub-seed
     5 + 7919 i) submitted as device tensors into one server with 4 builds in
     flight; plain or rotation-fitting leaves.  The arrival rate is set for
-    ~80 % offered load from a calibration build of each leaf size.  Reports
+    ~80 % offered load from calibration builds of each leaf size (a build's
+    time alone fitted as fixed + per-key cost).  Reports
     p50/p99 build latency (submit to finish), aggregate keys/s, how the
     requests' leaf-search kernels overlapped on the device (device-time
     intervals), and whether every result equals the same build alone.  With
@@ -658,15 +659,21 @@ def serve_run(pkg, requests: int, max_keys: float, rf: bool, rank: int = 0, chec
     reqs = [(shk_inputs.splitmix64_stream_torch(5 + 7919 * i + 1000003 * rank, int(sz), device="cuda"), int(n))
             for i, (sz, n) in enumerate(zip(sizes, leafs))]
     torch.cuda.synchronize()
-    # calibration: seconds per key of a build at each leaf size
-    per_key = {}
+    # calibration: a build's time alone as fixed + per-key cost at each leaf
+    # size, fitted to builds of 6*10^4 and 6*10^5 keys (small builds are
+    # dominated by fixed costs such as the retrieval solve's serial chain)
+    fixed, per_key = {}, {}
     for n in (48, 58):
-        k = shk_inputs.distinct_u64(60000, 77 + n)
-        pkg.shk_build(k, n, BUCKET, leaf_mode=mode).close()  # tuning / warm-up
-        t = time.perf_counter()
-        pkg.shk_build(k, n, BUCKET, leaf_mode=mode).close()
-        per_key[n] = (time.perf_counter() - t) / k.size
-    service = float(np.mean([k.numel() * per_key[n] for k, n in reqs]))
+        ts = []
+        for cnt in (60_000, 600_000):
+            k = shk_inputs.distinct_u64(cnt, 77 + n)
+            pkg.shk_build(k, n, BUCKET, leaf_mode=mode).close()  # tuning / warm-up
+            t = time.perf_counter()
+            pkg.shk_build(k, n, BUCKET, leaf_mode=mode).close()
+            ts.append(time.perf_counter() - t)
+        per_key[n] = max((ts[1] - ts[0]) / 540_000, 1e-12)
+        fixed[n] = max(ts[0] - 60_000 * per_key[n], 0.0)
+    service = float(np.mean([fixed[n] + k.numel() * per_key[n] for k, n in reqs]))
     rate = 0.8 / service
     gaps = -np.log(1.0 - shk_inputs.uniform01(55 + 1000 * rank, R)) / rate
     if burst:
@@ -713,7 +720,8 @@ def serve_run(pkg, requests: int, max_keys: float, rf: bool, rank: int = 0, chec
            "keys_per_s": total / span, "p50_ms": float(np.percentile(lat, 50)),
            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "all_ok": ok,
            "total_keys": total, "makespan_s": span, "arrival_rate_per_s": rate,
-           "calibration_s_per_key": per_key, "peak_reserved_bytes": st["peak_in_use_bytes"],
+           "calibration_s_per_key": per_key, "calibration_fixed_s": fixed,
+           "peak_reserved_bytes": st["peak_in_use_bytes"],
            "leaf_kernels": {"requests_overlapping_an_earlier_one": overlapping,
                             "busy_s_summed": busy / 1e9,
                             "first_start_to_last_end_s": (spans[-1][1] - spans[0][0]) / 1e9 if spans else 0.0}}
