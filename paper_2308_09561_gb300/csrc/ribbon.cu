@@ -346,7 +346,8 @@ __global__ void __launch_bounds__(kRibbonThreads)
 }
 
 // ---------------------------------------------------------------------------
-// 128-bit rows (leaf size n > 24): one warp per shard.
+// 128-bit rows (leaf size n > 24): one warp per (shard, seed) attempt; the
+// persistent warps and how they share out seeds are described at k_ribbon128.
 //
 // The keys are counting-sorted by start slot.  In ascending start order a
 // row starting at s only ever meets stored rows whose pivots lie in
@@ -357,8 +358,9 @@ __global__ void __launch_bounds__(kRibbonThreads)
 // The window is kept reduced: no stored row has a 1 in another stored row's
 // pivot column.  Reducing a new row X then takes one step instead of a walk
 // of ~25 dependent steps: X is XORed with the stored rows at exactly the
-// pivots where X itself has a 1, and the result's lowest set column is the
-// new pivot (a free column, since the result is 0 on every pivot column).
+// pivots where X itself has a 1, and the result's lowest set column (from
+// X's start, cyclically in the ring) is the new pivot (a free column, since
+// the result is 0 on every pivot column).
 // The new pivot column is then cleared from the stored rows that have it.
 // These extra row operations add rows of the system to rows of the system
 // with higher pivots, so the pivot set -- and the solution that is 0 on
@@ -368,7 +370,9 @@ __global__ void __launch_bounds__(kRibbonThreads)
 // held as 128 bit columns; lane L of the warp holds columns L, L + 32,
 // L + 64, L + 96, each 128 bits over the ring's rows.  One reduction is then
 // four column parities per lane and four ballots; occupancy and right-hand
-// sides of the ring's rows are 128-bit masks every lane holds.
+// sides of the ring's rows are 128-bit masks every lane holds.  Rows leave
+// the window in ring order (rotated into their pivot frame when the band is
+// read back for back substitution).
 // ---------------------------------------------------------------------------
 constexpr int kRib128Warps = 2;    // warps per CTA
 constexpr uint32_t kRib128Spec = 8;  // at most this many warps per shard (seed speculation)
